@@ -1,0 +1,263 @@
+"""Seeded synthetic workloads for the porous-media reactive LBM step.
+
+This module only generates inputs: physical parameters, seeded random fields
+and seeded mechanisms.  It contains none of the method's arithmetic (no
+equation of state, no equilibria, no unit conversion): both the CUDA library
+and the CPU oracle receive the same physical description and each derives its
+own lattice quantities from it.
+
+The paper's own workloads cannot be reproduced (the capillary experiment's
+fluxes and the SOFC mechanism are not available), so the generators below make
+inputs with the shapes of those cases:
+
+* ``capillary`` -- binary counter-diffusion in an open capillary (Sec. 5.1
+  uses a 1920-node 1-D tube at 300 K with reservoirs at both ends; the
+  synthetic case uses masses 4 and 40 g/mol).
+* ``slab`` -- a 2-D porous slab of the SOFC-electrode gas mixture
+  (H2/H2O/N2-like masses 2/18/28 g/mol at 1073.15 K, Sec. 5.2) with a seeded
+  Gaussian-random-field porosity.
+* ``anode3d`` -- the 3-D reactive electrode: gas plus surface-adsorbed species
+  with a seeded, element-balanced mass-action mechanism.
+* ``capillary_batch`` -- many independent capillaries of uneven length and
+  pressure.
+
+Node ordering everywhere is ``n = x + nx * (y + ny * z)`` (x fastest).
+"""
+from __future__ import annotations
+
+import dataclasses
+from typing import List, Optional
+
+import numpy as np
+
+ATM = 101325.0
+
+BC_PERIODIC = "periodic"
+BC_INLET = "inlet"
+BC_BOUNCEBACK = "bounceback"
+
+
+@dataclasses.dataclass
+class Mechanism:
+    """Mass-action surface mechanism on one catalytic surface.
+
+    Irreversible forward reactions; a reversible step is written as two
+    entries.  Stoichiometric coefficients are signed (products positive).
+    ``order_gas``/``order_surf`` are the reactant orders (the negative parts of
+    the stoichiometry).
+    """
+    S: int                      # surface species (including the empty site)
+    R: int                      # reactions
+    nu_gas: np.ndarray          # (R, M) signed stoichiometry of gas species
+    nu_surf: np.ndarray         # (R, S) signed stoichiometry of surface species
+    A: np.ndarray               # (R,) pre-exponential factors, SI for the order
+    Ea: np.ndarray              # (R,) activation energies [J/mol]
+    gamma: float                # site density Gamma [mol/m^2]
+    a_s: float                  # specific surface area a^(s) [1/m]
+    surf_molar_mass: np.ndarray  # (S,) [kg/mol] (adsorbate mass, empty site 0)
+    surf_cv_factor: np.ndarray   # (S,) C_v / (R_U / m) of the adsorbates
+    surf_U0: np.ndarray          # (S,) molar internal energy at T_thermo [J/mol]
+    gas_U0_molar: np.ndarray     # (M,) molar internal energy at T_thermo [J/mol]
+    elements_gas: np.ndarray     # (M, E) element counts of gas species
+    elements_surf: np.ndarray    # (S, E) element counts of adsorbates
+    Xs_init: np.ndarray          # (S,) initial coverages (uniform)
+
+
+@dataclasses.dataclass
+class Workload:
+    name: str
+    nx: int
+    ny: int
+    nz: int
+    bc_lo: str                  # x = 0 face
+    bc_hi: str                  # x = nx-1 face
+    M: int
+    energy: bool
+    knudsen: bool
+    dx: float                   # lattice spacing [m]
+    theta_max: float            # lattice temperature R_a T dt^2/dx^2 of the lightest species at T_scale
+    T_scale: float              # temperature that fixes dt [K]
+    T_ref: float                # reference state of D_ab and mu [K]
+    P_ref: float                # [Pa]
+    molar_mass: np.ndarray      # (M,) [kg/mol]
+    D_ref: np.ndarray           # (M, M) binary diffusivities at (T_ref, P_ref) [m^2/s]
+    mu_ref: np.ndarray          # (M,) species viscosities at T_ref [Pa s]
+    mu_exp: float               # mu_a ~ (T/T_ref)^mu_exp
+    Pr: float                   # Prandtl number
+    bulk_ratio: float           # bulk viscosity / shear viscosity
+    cv_factor: np.ndarray       # (M,) C_{v,a} / R_a
+    U0: np.ndarray              # (M,) specific internal energy at T_thermo [J/kg]
+    T_thermo: float             # [K]
+    tortuosity: float
+    pore_radius: float          # [m]
+    porosity: np.ndarray        # (N,)
+    X_init: np.ndarray          # (M, N) initial mole fractions
+    T_init: np.ndarray          # (N,) [K]
+    P_init: np.ndarray          # (N,) [Pa]
+    X_in_lo: np.ndarray         # (M,) reservoir composition at x = 0
+    X_in_hi: np.ndarray         # (M,) reservoir composition at x = nx-1
+    T_in_lo: float
+    T_in_hi: float
+    P_in_lo: float
+    P_in_hi: float
+    steps: int
+    mechanism: Optional[Mechanism] = None
+    U_init: Optional[np.ndarray] = None   # (D, N) initial velocity [m/s]; None: at rest
+
+    @property
+    def N(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    @property
+    def D(self) -> int:
+        return 3 if self.nz > 1 else 2
+
+    @property
+    def Q(self) -> int:
+        return 27 if self.D == 3 else 9
+
+    @property
+    def L(self) -> int:
+        """Number of lattices: M species + momentum (+ energy)."""
+        return self.M + 1 + (1 if self.energy else 0)
+
+
+# --------------------------------------------------------------------------
+# random fields
+# --------------------------------------------------------------------------
+
+def gaussian_random_field(shape, corr_len: float, seed: int) -> np.ndarray:
+    """Standardised periodic Gaussian random field with covariance
+    exp(-r^2 / (2 corr_len^2)), made by filtering white noise in Fourier space.
+    ``shape`` is given slowest-first, e.g. (nz, ny, nx)."""
+    rng = np.random.default_rng(seed)
+    noise = rng.standard_normal(shape)
+    k2 = np.zeros(shape)
+    for ax, n in enumerate(shape):
+        k = 2.0 * np.pi * np.fft.fftfreq(n)
+        sh = [1] * len(shape)
+        sh[ax] = n
+        k2 = k2 + (k.reshape(sh)) ** 2
+    # amplitude filter = sqrt of the Gaussian spectrum exp(-k^2 l^2 / 2)
+    filt = np.exp(-0.25 * k2 * corr_len ** 2)
+    field = np.real(np.fft.ifftn(np.fft.fftn(noise) * filt))
+    field -= field.mean()
+    sd = field.std()
+    return field / sd if sd > 0 else field
+
+
+def porosity_field(shape, corr_len: float, seed: int, mean=0.45, amp=0.1, lo=0.3, hi=0.6) -> np.ndarray:
+    z = gaussian_random_field(shape, corr_len, seed)
+    return np.clip(mean + amp * z, lo, hi).reshape(-1)
+
+
+def random_mole_fractions(M: int, N: int, seed: int, lo=0.1, hi=0.8) -> np.ndarray:
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(lo, hi, size=(M, N))
+    return x / x.sum(axis=0, keepdims=True)
+
+
+# --------------------------------------------------------------------------
+# species sets
+# --------------------------------------------------------------------------
+
+def _he_ar():
+    m = np.array([4.0e-3, 40.0e-3])
+    D = np.array([[0.0, 7.0e-5], [7.0e-5, 0.0]])      # He-Ar at 300 K, 1 atm
+    mu = np.array([1.99e-5, 2.27e-5])                  # at 300 K
+    cv = np.array([1.5, 1.5])
+    return m, D, mu, cv
+
+
+def _h2_h2o_n2():
+    m = np.array([2.0e-3, 18.0e-3, 28.0e-3])
+    D = np.array([[0.0, 8.0e-4, 7.5e-4],
+                  [8.0e-4, 0.0, 2.5e-4],
+                  [7.5e-4, 2.5e-4, 0.0]])             # at 1073.15 K, 1 atm
+    mu = np.array([2.0e-5, 4.0e-5, 4.2e-5])           # at 1073.15 K
+    cv = np.array([2.5, 3.0, 2.5])
+    return m, D, mu, cv
+
+
+# --------------------------------------------------------------------------
+# workloads
+# --------------------------------------------------------------------------
+
+def capillary(nx=256, ny=4, P=ATM, T=300.0, pore_radius=1.0e-6, dx=1.0e-6,
+              steps=2000, knudsen=True, theta_max=1.0 / 3.0, name=None,
+              split=True, X_lo=(1.0, 0.0), X_hi=(0.0, 1.0)) -> Workload:
+    """Binary counter-diffusion of masses 4 and 40 g/mol in an open capillary
+    (porosity 1, tortuosity 1), isothermal, with reservoirs of pure A at x = 0
+    and pure B at x = nx-1; the left half starts as A and the right half as B
+    (the split initial state of the capillary experiment, Sec. 5.1)."""
+    m, D, mu, cv = _he_ar()
+    N = nx * ny
+    X = np.zeros((2, N))
+    xs = np.tile(np.arange(nx), ny)
+    X_lo = np.asarray(X_lo, float)
+    X_hi = np.asarray(X_hi, float)
+    if split:
+        X[:, xs < nx // 2] = X_lo[:, None]
+        X[:, xs >= nx // 2] = X_hi[:, None]
+    else:
+        X[:] = 0.5
+    return Workload(
+        name=name or f"capillary_{nx}x{ny}", nx=nx, ny=ny, nz=1,
+        bc_lo=BC_INLET, bc_hi=BC_INLET, M=2, energy=False, knudsen=knudsen,
+        dx=dx, theta_max=theta_max, T_scale=T, T_ref=300.0, P_ref=ATM,
+        molar_mass=m, D_ref=D, mu_ref=mu, mu_exp=0.7, Pr=0.7, bulk_ratio=1.0,
+        cv_factor=cv, U0=np.zeros(2), T_thermo=0.0, tortuosity=1.0,
+        pore_radius=pore_radius, porosity=np.ones(N), X_init=X,
+        T_init=np.full(N, T), P_init=np.full(N, P),
+        X_in_lo=X_lo, X_in_hi=X_hi, T_in_lo=T, T_in_hi=T, P_in_lo=P, P_in_hi=P,
+        steps=steps)
+
+
+def slab(nx=512, ny=512, seed_phi=2, seed_X=1, steps=5000, dx=0.25e-6,
+         energy=True, bc_x=BC_PERIODIC, X_lo=None, X_hi=None, name=None,
+         theta_max=1.0 / 3.0) -> Workload:
+    """2-D porous slab of a three-species mixture (masses 2, 18, 28 g/mol) at
+    1073.15 K and 1 atm; porosity is a seeded Gaussian random field
+    (correlation length 16 nodes) clipped to [0.3, 0.6]; tortuosity 3; pore
+    radius 0.5 um; mole fractions seeded uniform in [0.1, 0.8] per node, then
+    normalised.  With ``bc_x='inlet'`` the x faces are reservoirs."""
+    m, D, mu, cv = _h2_h2o_n2()
+    N = nx * ny
+    T = 1073.15
+    phi = porosity_field((ny, nx), 16.0, seed_phi)
+    X = random_mole_fractions(3, N, seed_X)
+    X_lo = np.asarray(X_lo if X_lo is not None else [1 / 3, 1 / 3, 1 / 3], float)
+    X_hi = np.asarray(X_hi if X_hi is not None else [1 / 3, 1 / 3, 1 / 3], float)
+    return Workload(
+        name=name or f"slab_{nx}x{ny}", nx=nx, ny=ny, nz=1, bc_lo=bc_x, bc_hi=bc_x,
+        M=3, energy=energy, knudsen=True, dx=dx, theta_max=theta_max, T_scale=T,
+        T_ref=T, P_ref=ATM, molar_mass=m, D_ref=D, mu_ref=mu, mu_exp=0.7,
+        Pr=0.7, bulk_ratio=1.0, cv_factor=cv, U0=np.zeros(3), T_thermo=0.0,
+        tortuosity=3.0, pore_radius=0.5e-6, porosity=phi, X_init=X,
+        T_init=np.full(N, T), P_init=np.full(N, ATM),
+        X_in_lo=X_lo, X_in_hi=X_hi, T_in_lo=T, T_in_hi=T, P_in_lo=ATM, P_in_hi=ATM,
+        steps=steps)
+
+
+def adjoint_slab(nx=256, ny=256, steps=1000, name=None) -> Workload:
+    """The slab statistics with H2-rich and H2-lean reservoirs on the x faces
+    (periodic in y): the setting of the outlet-flux gradient problem."""
+    return slab(nx=nx, ny=ny, seed_phi=6, seed_X=7, steps=steps, bc_x=BC_INLET,
+                X_lo=[0.8, 0.1, 0.1], X_hi=[0.1, 0.45, 0.45],
+                name=name or f"adjoint_slab_{nx}x{ny}")
+
+
+def capillary_batch(n_cases=64, seed=5, ny=4, steps=2000, nmin=128, nmax=4096) -> List[Workload]:
+    """Independent capillaries: lengths log-uniform in [nmin, nmax] nodes,
+    pressures log-uniform in [0.01, 10] atm, pore radius log-uniform in
+    [0.1, 10] um, masses 4 and 40 g/mol, 300 K."""
+    rng = np.random.default_rng(seed)
+    lens = np.exp(rng.uniform(np.log(nmin), np.log(nmax), n_cases)).astype(int)
+    Ps = np.exp(rng.uniform(np.log(0.01), np.log(10.0), n_cases)) * ATM
+    rps = np.exp(rng.uniform(np.log(0.1e-6), np.log(10e-6), n_cases))
+    out = []
+    for c in range(n_cases):
+        out.append(capillary(nx=int(lens[c]), ny=ny, P=float(Ps[c]),
+                             pore_radius=float(rps[c]), steps=steps,
+                             name=f"case{c}_{int(lens[c])}x{ny}"))
+    return out

@@ -1,0 +1,337 @@
+"""Benchmark of the fused porous-media LBM step on GB300.
+
+Default workload: the 2-D porous slab, 512 x 512 nodes, three species
+(2/18/28 g/mol), energy lattice on, Knudsen on, FP32 populations, periodic;
+5 lattices x 9 velocities per node.  One bench "step" is one full time step
+of the hot path (stream, moments, gradients, diffusion-velocity solve,
+species / momentum / energy collisions) over the whole lattice.
+
+Timing: W untimed warm-up steps, then K timed steps; the 94 MB state fits in
+L2, so L2 is flushed (a 256 MB device write) before every timed step and each
+step is timed alone with CUDA events on the library's stream.  The value is
+species-weighted MLUPS (node updates per second x lattices) summed over the
+ranks.  With --gpus N > 1 (torchrun) every rank runs its own replica of the
+workload (weak scaling, no data-path collective).
+
+--impl reference times the FP64 CPU oracle (the test-side checker, as it
+stands) on a 64 x 64 sample of the same workload per step, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2409_02930_gb300 import workloads as W  # noqa: E402
+
+METRIC = "species-weighted MLUPS"
+UNIT = "MLUPS (node updates/s x lattices, 1e6)"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def algorithmic_bytes_per_node(wl, real_bytes):
+    """Populations read once and written once, plus the porosity."""
+    return wl.L * wl.Q * real_bytes * 2 + real_bytes
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_baseline(wl_sample, seconds=10.0):
+    """Time the FP64 oracle as it stands on a bounded sample (all host cores)."""
+    import oracle
+    o = oracle.Oracle(wl_sample)
+    t0 = time.perf_counter()
+    o.step(1)
+    t1 = time.perf_counter() - t0
+    n = max(1, int(seconds / max(t1, 1e-6)))
+    t0 = time.perf_counter()
+    o.step(n)
+    el = time.perf_counter() - t0
+    mlups = wl_sample.N * n * wl_sample.L / el / 1e6
+    return {"value": mlups, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+            "sample": f"{wl_sample.name}: {n} FP64 oracle steps on {wl_sample.N} nodes, {el:.1f} s"}
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+    from paper_2409_02930_gb300 import lbm
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    wl = W.slab(nx=args.nx, ny=args.ny, steps=args.steps)
+    prec = lbm.LBM_FP32 if args.precision == "fp32" else lbm.LBM_FP64
+    rbytes = 4 if prec == lbm.LBM_FP32 else 8
+    g = lbm.Lattice(wl, precision=prec, stream=__import__("ctypes").c_void_p(stream.cuda_stream))
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    def one_step_timed():
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.step(1)
+        e1.record(stream)
+        return e0, e1
+
+    for _ in range(args.warmup):
+        one_step_timed()
+    torch.cuda.synchronize()
+    g.sync()
+
+    clocks = Clocks(local)
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)                                   # let the sampler start
+    lib = lbm.load()
+    lib.lbm_set_timing(g._h, 1)
+    t_wall = time.perf_counter()
+    evs = [one_step_timed() for _ in range(args.steps)]
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    barrier(ws)
+    clk = clocks.stop()
+    step_ms = sum(a.elapsed_time(b) for a, b in evs)
+    ms = (np.zeros(3)).astype(np.float64)
+    cnt = np.zeros(3, dtype=np.int64)
+    lib.lbm_get_timing(g._h, ms.ctypes.data_as(lbm._dp),
+                       cnt.ctypes.data_as(__import__("ctypes").POINTER(__import__("ctypes").c_longlong)))
+    lib.lbm_set_timing(g._h, 0)
+    g.sync()
+    step_ms_max = allreduce_max(ws, step_ms)
+
+    N, L = wl.N, wl.L
+    value = ws * N * L * args.steps / (step_ms_max / 1e3) / 1e6
+    # roofline of the dominant kernel (kind 1: collide / fused step)
+    per_launch_ms = ms[1] / max(cnt[1], 1)
+    alg_bytes = algorithmic_bytes_per_node(wl, rbytes) * N
+    peak, peak_kind = peaks()
+    achieved = alg_bytes / (per_launch_ms / 1e3) / 1e9
+    step_kernel_ms = (ms[0] + ms[1]) / max(cnt[1], 1)
+
+    # end to end through the C ABI with host buffers: H2D state, step, D2H state
+    host = torch.empty(g.population_bytes(), dtype=torch.uint8, pin_memory=True)
+    lib.lbm_get_populations(g._h, __import__("ctypes").c_void_p(host.data_ptr()), host.numel(), 0)
+    e2e_steps = max(10, min(args.steps, 200))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        lib.lbm_set_populations(g._h, __import__("ctypes").c_void_p(host.data_ptr()), host.numel(), 0)
+        g.step(1)
+        lib.lbm_get_populations(g._h, __import__("ctypes").c_void_p(host.data_ptr()), host.numel(), 0)
+    torch.cuda.synchronize()
+    e2e_s = allreduce_max(ws, time.perf_counter() - t0)
+    e2e_value = ws * N * L * e2e_steps / e2e_s / 1e6
+
+    # plain FP64 GPU step beside the FP32 form, same workload
+    extra = {}
+    if rank == 0 and prec == lbm.LBM_FP32 and not args.no_fp64:
+        g64 = lbm.Lattice(wl, precision=lbm.LBM_FP64, stream=__import__("ctypes").c_void_p(stream.cuda_stream))
+        n64 = max(3, min(50, args.steps // 20))
+        for _ in range(3):
+            g64.step(1)
+        torch.cuda.synchronize()
+        ev = [one_step_timed_of(g64, flush, stream, torch) for _ in range(n64)]
+        torch.cuda.synchronize()
+        t64 = sum(a.elapsed_time(b) for a, b in ev) / n64
+        extra["fp64_step"] = {"ms_per_step": t64, "value": N * L / (t64 / 1e3) / 1e6, "unit": UNIT,
+                              "bound": "fp64 alu"}
+        # FP32 vs FP64 GPU after the same number of steps from the same state
+        nerr = 200
+        a32 = lbm.Lattice(wl, precision=lbm.LBM_FP32)
+        a64 = lbm.Lattice(wl, precision=lbm.LBM_FP64)
+        a32.step(nerr)
+        a64.step(nerr)
+        errs = {}
+        for nm in ("RHO_A", "J_A", "T"):
+            k = getattr(lbm, "LBM_MOM_" + nm)
+            x, y = a32.moments(k), a64.moments(k)
+            errs[nm] = float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
+        extra["fp32_vs_fp64_after_%d_steps" % nerr] = errs
+        g64.close(); a32.close(); a64.close()
+
+    out = None
+    if rank == 0:
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.precision.replace("fp", "f"),
+            "data": "synthetic (seeded porosity field and compositions)",
+            "config": {"workload": f"slab_{args.nx}x{args.ny}_M3_energy_knudsen_{args.precision}",
+                       "nodes": N, "lattices": L, "velocities": wl.Q, "parallelism": f"replicas x{ws}",
+                       "l2": "flushed (256 MB write) before every timed step"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "kernel": "collide" if cnt[0] > 0 else "fused_step",
+                         "kernel_ms": per_launch_ms, "step_kernels_ms": step_kernel_ms,
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "bytes_per_node": algorithmic_bytes_per_node(wl, rbytes)},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": g.population_bytes(),
+                    "d2h_bytes_per_step": g.population_bytes(), "steps": e2e_steps},
+            "gpu_launches": int(cnt[0] + cnt[1]),
+            "clocks": clk,
+            "wall_s": t_wall,
+        }
+        out.update(extra)
+        if ws == 1 and not args.no_cpu:
+            out["cpu_baseline"] = cpu_baseline(W.slab(nx=128, ny=128, steps=1, name="slab_128x128_sample"),
+                                               seconds=args.cpu_seconds)
+    g.close()
+    return out
+
+
+def one_step_timed_of(g, flush, stream, torch):
+    flush.zero_()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(1)
+    e1.record(stream)
+    return e0, e1
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import oracle
+    wl = W.slab(nx=64, ny=64, steps=1, name="slab_64x64_sample")
+    o = oracle.Oracle(wl)
+    o.step(args.warmup)
+    t0 = time.perf_counter()
+    o.step(args.steps)
+    el = time.perf_counter() - t0
+    value = wl.N * wl.L * args.steps / el / 1e6
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded porosity field and compositions)",
+            "config": {"workload": f"slab_{args.nx}x{args.ny}_M3_energy_knudsen_{args.precision}",
+                       "sample_per_step": "64x64 nodes of the same statistics", "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.threads(), "kind": "oracle",
+                             "sample": f"{args.steps} oracle steps of a 64x64 sample, {el:.1f} s"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--nx", type=int, default=512)
+    ap.add_argument("--ny", type=int, default=512)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    ws, rank, local = dist_init()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

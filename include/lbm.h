@@ -1,0 +1,194 @@
+/*
+ * lbm.h -- C ABI of the GB300 library for the mean-field lattice Boltzmann
+ * step of reactive gas mixtures in homogenised porous media
+ * (N. Sawant and I. V. Karlin, "Mean field lattice Boltzmann model for
+ * reactive mixtures in porous media", arXiv 2409.02930).
+ *
+ * One call of lbm_step advances every node by one fused stream-and-collide
+ * time step: the M species lattices (Sec. 2.3, eqn:finalNumericalEquationsReactive
+ * with the dusty-gas relaxation eqn:fStar and the diffusion-velocity system
+ * eqn:transform1), the mixture momentum lattice (Sec. 3.2, eqn:f with the
+ * extended equilibrium eq:feqmix and the net Knudsen force
+ * eqn:netKnudsenForce), the mixture energy lattice (Sec. 3.3, eqn:g with
+ * eq:geq_i and eq:gstar) and, when a surface mechanism is given, the
+ * heterogeneous-reaction sources of Sec. 4.2 (eq:rho_pc, eqn:f_source,
+ * eqn:g_source, eq:fsourceHetero).
+ *
+ * Conventions
+ *   - All functions return LBM_OK (0) or a negative status code; no C++
+ *     exception crosses this boundary.  lbm_last_error() describes the last
+ *     failure of a context (or of lbm_create when ctx is NULL).
+ *   - The library owns every device buffer it allocates; the caller owns
+ *     every buffer it passes in.  Host arrays in lbm_config are read during
+ *     lbm_create only and may be freed afterwards.
+ *   - Work is issued on the stream given in lbm_config (NULL: the legacy
+ *     default stream) and is asynchronous unless stated otherwise.
+ *   - Node order is n = x + nx*(y + ny*z), x fastest.  Populations are stored
+ *     structure-of-arrays [lattice][i][n]; lattice 0..M-1 are the species,
+ *     M the momentum lattice, M+1 the energy lattice (when on).  Velocity i
+ *     has c = (i%3-1, (i/3)%3-1, i/9-1) (D3Q27) or (i%3-1, i/3-1, 0) (D2Q9).
+ *   - Internally velocities, temperatures R*T, diffusivities and pressures are
+ *     in lattice units (dx, dt); densities stay in kg/m^3.  dt is fixed so
+ *     that the lightest species has R_a T_scale dt^2/dx^2 = theta_max.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+#define LBM_OK            0
+#define LBM_ERR_ARG      -1   /* invalid argument or configuration */
+#define LBM_ERR_ALLOC    -2   /* device or host allocation failed */
+#define LBM_ERR_NUMERIC  -3   /* non-finite or negative density seen by a kernel */
+#define LBM_ERR_TIMEOUT  -4   /* a bounded device wait gave up */
+#define LBM_ERR_STATE    -5   /* call not valid in the context's state */
+#define LBM_ERR_CUDA     -6   /* a CUDA runtime call failed */
+
+/* boundary conditions of the two x faces (y and z are periodic) */
+#define LBM_BC_PERIODIC   0
+#define LBM_BC_INLET      1   /* reservoir: missing populations replaced by equilibria */
+#define LBM_BC_BOUNCEBACK 2   /* missing populations reflected (no flux, no slip) */
+
+/* precision of storage and relaxation */
+#define LBM_FP64 0
+#define LBM_FP32 1            /* FP32 storage and arithmetic; the diffusion-velocity
+                                 solve switches to FP64 where its condition bound
+                                 exceeds kappa_threshold */
+
+/* moment selectors for lbm_moments (layout [component][n]) */
+#define LBM_MOM_RHO_A 0       /* species densities rho_a, [M][N], kg/m^3 (eq:density1) */
+#define LBM_MOM_J_A   1       /* species momenta sum_i f_ai c_i, [M][D][N], lattice units (eq:momentum1) */
+#define LBM_MOM_RHO   2       /* mixture density of the momentum lattice, [N], kg/m^3 (eqn:fdensity) */
+#define LBM_MOM_U     3       /* mixture velocity, [D][N], lattice units (eqn:f1momMomentum) */
+#define LBM_MOM_T     4       /* temperature, [N], K (eq:temperature) */
+#define LBM_MOM_P     5       /* pressure, [N], Pa (eqn:eosIdealGas) */
+#define LBM_MOM_V_A   6       /* diffusion velocities V_a, [M][D][N], lattice units (eqn:transform1) */
+#define LBM_MOM_N_A   7       /* molar fluxes rho_a (u + V_a)/m_a, [M][D][N], mol m^-2 s^-1 */
+#define LBM_MOM_XS    8       /* surface coverages X^(s), [S][N] (eq:surfaceMoleFractions) */
+#define LBM_MOM_RHO_S 9       /* sum_a rho_a, [N], kg/m^3 (eq:rhoSpec) */
+
+typedef struct lbm_ctx lbm_ctx;
+
+/*
+ * Physical description of one lattice.  Arrays are host pointers, double
+ * precision, SI units unless stated; N = nx*ny*nz.
+ */
+typedef struct lbm_config {
+  int nx, ny, nz;              /* nz == 1: D2Q9, nz > 1: D3Q27 */
+  int bc_lo, bc_hi;            /* LBM_BC_* of the x = 0 and x = nx-1 faces */
+  int M;                       /* gas species: 2, 3 or 6 */
+  int energy;                  /* 1: energy lattice on; 0: isothermal at T_init */
+  int knudsen;                 /* 1: Knudsen diffusion on */
+  int precision;               /* LBM_FP64 or LBM_FP32 */
+  double dx;                   /* lattice spacing [m] */
+  double theta_max;            /* lattice temperature of the lightest species at T_scale */
+  double T_scale;              /* [K] */
+  double T_ref, P_ref;         /* reference state of D_ref and mu_ref [K], [Pa] */
+  double mu_exp;               /* mu_a = mu_ref,a (T/T_ref)^mu_exp */
+  double Pr;                   /* Prandtl number: lambda = mu C_p / Pr */
+  double bulk_ratio;           /* bulk viscosity / shear viscosity */
+  double T_thermo;             /* reference temperature of U0 [K] */
+  double tortuosity;
+  double pore_radius;          /* [m]; Knudsen diameter d0 = 2 pore_radius */
+  double kappa_threshold;      /* LBM_FP32: FP64 solve above this bound (<= 0: 1e3) */
+  const double* molar_mass;    /* [M] kg/mol */
+  const double* D_ref;         /* [M*M] binary diffusivities at (T_ref, P_ref) [m^2/s] */
+  const double* mu_ref;        /* [M] Pa s at T_ref */
+  const double* cv_factor;     /* [M] C_v,a / R_a */
+  const double* U0;            /* [M] specific internal energy at T_thermo [J/kg] */
+  const double* porosity;      /* [N] in (0, 1] */
+  const double* X_init;        /* [M*N] initial mole fractions */
+  const double* T_init;        /* [N] initial (isothermal: fixed) temperature [K] */
+  const double* P_init;        /* [N] initial pressure [Pa] */
+  const double* U_init;        /* [3*N] initial velocity [m/s], or NULL for rest */
+  const double* X_in_lo;       /* [M] reservoir composition at x = 0 (LBM_BC_INLET) */
+  const double* X_in_hi;       /* [M] reservoir composition at x = nx-1 */
+  double T_in_lo, T_in_hi, P_in_lo, P_in_hi;
+  /* surface mechanism (Sec. 4): S == 0 for none */
+  int S, R;                    /* surface species (<= 12), reactions (<= 32) */
+  const double* nu_gas;        /* [R*M] signed stoichiometry, gas */
+  const double* nu_surf;       /* [R*S] signed stoichiometry, surface */
+  const double* A_pre;         /* [R] Arrhenius prefactors (SI for the order) */
+  const double* Ea;            /* [R] activation energies [J/mol] */
+  double gamma;                /* site density [mol/m^2] */
+  double a_s;                  /* specific surface area [1/m] */
+  const double* surf_cv_factor;/* [S] molar C_v / R_U of the adsorbates */
+  const double* surf_U0;       /* [S] molar internal energy at T_thermo [J/mol] */
+  const double* Xs_init;       /* [S] initial coverages */
+  void* stream;                /* cudaStream_t for all work of the context */
+} lbm_config;
+
+/*
+ * lbm_create -- validate cfg, allocate device state and set every population
+ * to the equilibrium of the initial fields (eq:27eq, eq:feqmix without
+ * extension, eq:geq_i).  On success *out holds a new context.
+ * Errors: LBM_ERR_ARG (dimensions < 1, inlet face with nx < 3, M outside
+ * {2, 3, 6}, porosity outside (0, 1], non-positive mass, temperature, pressure,
+ * dx or theta_max), LBM_ERR_ALLOC, LBM_ERR_CUDA (no device).
+ */
+int lbm_create(lbm_ctx** out, const lbm_config* cfg);
+
+/*
+ * lbm_step -- advance n_steps time steps (pull streaming with the boundary
+ * conditions, moments, isotropic gradients, diffusion-velocity solve,
+ * species / momentum / energy collisions and surface source), asynchronously
+ * on the context's stream.  Returns the status recorded by kernels of earlier
+ * steps (LBM_ERR_NUMERIC if a non-finite density was seen) or LBM_OK.
+ */
+int lbm_step(lbm_ctx* ctx, int n_steps);
+
+/*
+ * lbm_moments -- macroscopic fields of the current state, as the next step
+ * would see them (streamed populations, boundary conditions applied); the
+ * state is not changed.  out is caller-owned, bytes its size; out_on_device
+ * says whether out is a device pointer.  Values are written as double
+ * (layouts per LBM_MOM_*).  The call synchronises the stream when out is a
+ * host pointer.  Errors: LBM_ERR_ARG (unknown selector, buffer too small).
+ */
+int lbm_moments(lbm_ctx* ctx, int which, void* out, size_t bytes, int out_on_device);
+
+/*
+ * lbm_get_populations / lbm_set_populations -- copy the stored populations
+ * (post-collision state, [L][Q][N] in the context's precision: 8 bytes per
+ * value for LBM_FP64, 4 for LBM_FP32) to / from a caller buffer (host when
+ * on_device == 0).  Synchronous.  Errors: LBM_ERR_ARG when bytes differs
+ * from lbm_population_bytes().
+ */
+size_t lbm_population_bytes(const lbm_ctx* ctx);
+int lbm_get_populations(lbm_ctx* ctx, void* buf, size_t bytes, int on_device);
+int lbm_set_populations(lbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
+
+/* lbm_sync -- wait for the context's stream; returns the device status. */
+int lbm_sync(lbm_ctx* ctx);
+
+/* lbm_info -- dt [s], dx/dt [m/s], lattices L, velocities Q, dimension D into out[0..4]. */
+int lbm_info(const lbm_ctx* ctx, double* out5);
+
+/*
+ * lbm_set_timing / lbm_get_timing -- kernel timing with CUDA events recorded
+ * on the context's stream around every kernel that lbm_step launches.
+ * lbm_set_timing(ctx, 1) clears and starts recording (at most 65536 launches
+ * are kept); lbm_get_timing synchronises the stream and returns, per kernel
+ * kind (0: macro-field pass, 1: collide / fused step, 2: reserved), the summed
+ * device milliseconds and the launch counts.  Errors: LBM_ERR_STATE when
+ * timing is off.
+ */
+int lbm_set_timing(lbm_ctx* ctx, int enable);
+int lbm_get_timing(lbm_ctx* ctx, double* ms_by_kind /* [3] */, long long* launches_by_kind /* [3] */);
+
+/* lbm_destroy -- free the context (synchronises its stream first). NULL is a no-op. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* lbm_last_error -- message of the last failure (ctx may be NULL). */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

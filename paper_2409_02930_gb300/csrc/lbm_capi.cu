@@ -1,0 +1,474 @@
+// Host side of the C ABI declared in include/lbm.h: configuration checks,
+// lattice-unit conversion, device allocation and the per-step launches.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+#include "lbm_kernels.cuh"
+#include "lbm_ops.h"
+
+namespace {
+
+const double R_UNIV_SI = 8.314462618;   // J/(mol K)
+const double PI_SI = 3.14159265358979323846;
+
+thread_local std::string g_create_error;
+
+}  // namespace
+
+struct lbm_ctx {
+  int nx, ny, nz, N, D, Q, M, L, energy, knudsen, precision, S;
+  double dt, cvel;
+  cudaStream_t stream;
+  void* pops[2];
+  int cur;
+  void* phi;
+  void* Tfix;
+  void* mac;
+  int* status;
+  double* scratch_out;        // device buffer for lbm_moments to host
+  size_t scratch_bytes;
+  lbm::Params<double> pd;
+  lbm::Params<float> pf;
+  lbm::InletTables<double> itd;
+  lbm::InletTables<float> itf;
+  lbm::Ops<double> od;
+  lbm::Ops<float> of;
+  std::string err;
+  // kernel timing (lbm_set_timing)
+  int timing;
+  std::vector<cudaEvent_t> ev;       // start/stop pairs
+  std::vector<int> ev_kind;
+  size_t ev_used;
+};
+
+namespace {
+
+int fail(lbm_ctx* c, int code, const std::string& msg) {
+  if (c) c->err = msg;
+  else g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, LBM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+size_t real_size(const lbm_ctx* c) { return c->precision == LBM_FP64 ? 8 : 4; }
+
+template <class R>
+void convert_params(const lbm::Params<double>& d, lbm::Params<R>& r) {
+  r.nx = d.nx; r.ny = d.ny; r.nz = d.nz; r.N = d.N;
+  r.bc_lo = d.bc_lo; r.bc_hi = d.bc_hi; r.knudsen = d.knudsen;
+  r.RU = (R)d.RU;
+  for (int a = 0; a < lbm::MMAX; ++a) {
+    r.m[a] = (R)d.m[a]; r.Ra[a] = (R)d.Ra[a]; r.muref[a] = (R)d.muref[a];
+    r.cvR[a] = (R)d.cvR[a]; r.U0[a] = (R)d.U0[a]; r.knc[a] = (R)d.knc[a];
+    for (int b = 0; b < lbm::MMAX; ++b) r.invDmm[a][b] = (R)d.invDmm[a][b];
+    r.rho_in[0][a] = (R)d.rho_in[0][a]; r.rho_in[1][a] = (R)d.rho_in[1][a];
+  }
+  r.mu_exp = (R)d.mu_exp; r.inv_Pr = (R)d.inv_Pr; r.bulk_ratio = (R)d.bulk_ratio;
+  r.T_thermo = (R)d.T_thermo; r.inv_T_ref = (R)d.inv_T_ref; r.Pref = (R)d.Pref;
+  r.T_in[0] = (R)d.T_in[0]; r.T_in[1] = (R)d.T_in[1];
+  r.kappa_thr = (R)d.kappa_thr;
+}
+
+template <class R>
+void convert_inlet(const lbm::InletTables<double>& d, lbm::InletTables<R>& r) {
+  for (int s = 0; s < 2; ++s) {
+    for (int a = 0; a < lbm::MMAX; ++a) r.rho[s][a] = (R)d.rho[s][a];
+    r.rho_sum[s] = (R)d.rho_sum[s]; r.Rmix[s] = (R)d.Rmix[s]; r.Umix[s] = (R)d.Umix[s]; r.T[s] = (R)d.T[s];
+  }
+}
+
+int validate(const lbm_config* c) {
+  if (!c) return fail(nullptr, LBM_ERR_ARG, "null config");
+  if (c->nx < 1 || c->ny < 1 || c->nz < 1) return fail(nullptr, LBM_ERR_ARG, "lattice dimensions must be >= 1");
+  if ((double)c->nx * c->ny * c->nz > 2.0e9) return fail(nullptr, LBM_ERR_ARG, "lattice too large");
+  if (c->M != 2 && c->M != 3 && c->M != 6) return fail(nullptr, LBM_ERR_ARG, "M must be 2, 3 or 6");
+  for (int s = 0; s < 2; ++s) {
+    int bc = s ? c->bc_hi : c->bc_lo;
+    if (bc < 0 || bc > 2) return fail(nullptr, LBM_ERR_ARG, "unknown boundary condition");
+    if (bc == LBM_BC_INLET && c->nx < 3) return fail(nullptr, LBM_ERR_ARG, "inlet faces need nx >= 3");
+    if (bc != LBM_BC_PERIODIC && c->nx < 2) return fail(nullptr, LBM_ERR_ARG, "walls need nx >= 2");
+  }
+  if ((c->bc_lo == LBM_BC_PERIODIC) != (c->bc_hi == LBM_BC_PERIODIC))
+    return fail(nullptr, LBM_ERR_ARG, "x faces must be both periodic or both non-periodic");
+  if (c->precision != LBM_FP64 && c->precision != LBM_FP32) return fail(nullptr, LBM_ERR_ARG, "unknown precision");
+  if (!(c->dx > 0) || !(c->theta_max > 0) || !(c->theta_max < 1) || !(c->T_scale > 0) || !(c->T_ref > 0) ||
+      !(c->P_ref > 0) || !(c->Pr > 0))
+    return fail(nullptr, LBM_ERR_ARG, "dx, theta_max in (0,1), T_scale, T_ref, P_ref and Pr must be positive");
+  if (c->knudsen && (!(c->pore_radius > 0) || !(c->tortuosity > 0)))
+    return fail(nullptr, LBM_ERR_ARG, "Knudsen diffusion needs a positive pore radius and tortuosity");
+  if (!c->molar_mass || !c->D_ref || !c->mu_ref || !c->cv_factor || !c->U0 || !c->porosity || !c->X_init ||
+      !c->T_init || !c->P_init)
+    return fail(nullptr, LBM_ERR_ARG, "missing input array");
+  for (int a = 0; a < c->M; ++a) {
+    if (!(c->molar_mass[a] > 0) || !(c->mu_ref[a] >= 0) || !(c->cv_factor[a] > 0))
+      return fail(nullptr, LBM_ERR_ARG, "molar masses and heat capacities must be positive");
+    for (int b = 0; b < c->M; ++b)
+      if (a != b && !(c->D_ref[a * c->M + b] > 0))
+        return fail(nullptr, LBM_ERR_ARG, "binary diffusivities must be positive");
+  }
+  size_t N = (size_t)c->nx * c->ny * c->nz;
+  for (size_t n = 0; n < N; ++n) {
+    if (!(c->porosity[n] > 0) || !(c->porosity[n] <= 1)) return fail(nullptr, LBM_ERR_ARG, "porosity outside (0, 1]");
+    if (!(c->T_init[n] > 0) || !(c->P_init[n] > 0)) return fail(nullptr, LBM_ERR_ARG, "non-positive T or P");
+  }
+  if (c->bc_lo == LBM_BC_INLET || c->bc_hi == LBM_BC_INLET) {
+    if (!c->X_in_lo || !c->X_in_hi || !(c->T_in_lo > 0) || !(c->T_in_hi > 0) || !(c->P_in_lo > 0) ||
+        !(c->P_in_hi > 0))
+      return fail(nullptr, LBM_ERR_ARG, "inlet faces need reservoir composition, T and P");
+  }
+  if (c->S != 0) return fail(nullptr, LBM_ERR_ARG, "surface mechanisms are not supported by this build");
+  return LBM_OK;
+}
+
+}  // namespace
+
+namespace lbm {
+
+// Lattice-unit parameters of a validated configuration.
+void make_params(const lbm_config* c, Params<double>& p, InletTables<double>& it, double& dt, double& cvel) {
+  const int M = c->M;
+  const int knudsen = c->knudsen ? 1 : 0;
+  // lattice units: max_a R_a T_scale dt^2/dx^2 = theta_max
+  double mmin = 1e300;
+  for (int a = 0; a < M; ++a) mmin = std::fmin(mmin, c->molar_mass[a]);
+  dt = c->dx * std::sqrt(c->theta_max * mmin / (R_UNIV_SI * c->T_scale));
+  cvel = c->dx / dt;
+  const double c2 = cvel * cvel;
+  std::memset(&p, 0, sizeof(p));
+  p.nx = c->nx; p.ny = c->ny; p.nz = c->nz; p.N = c->nx * c->ny * c->nz;
+  p.bc_lo = c->bc_lo; p.bc_hi = c->bc_hi; p.knudsen = knudsen;
+  p.RU = R_UNIV_SI / c2;
+  const double d0 = 2.0 * c->pore_radius / c->dx;
+  for (int a = 0; a < M; ++a) p.m[a] = c->molar_mass[a];
+  for (int a = 0; a < M; ++a) {
+    p.Ra[a] = p.RU / p.m[a];
+    p.muref[a] = c->mu_ref[a] / (cvel * c->dx);
+    p.cvR[a] = c->cv_factor[a] * p.Ra[a];
+    p.U0[a] = c->U0[a] / c2;
+    for (int b = 0; b < M; ++b)
+      p.invDmm[a][b] = (a == b) ? 0.0 : 1.0 / ((c->D_ref[a * M + b] / (cvel * c->dx)) * p.m[a] * p.m[b]);
+    // D^k = (phi/tortuosity)(d0/3) sqrt(8 R_U T/(pi m_a)); 1/tau^k = R_U T/(D^k m_a)
+    if (knudsen)
+      p.knc[a] = 3.0 * c->tortuosity * p.RU / (d0 * p.m[a] * std::sqrt(8.0 * p.RU / (PI_SI * p.m[a])));
+  }
+  p.mu_exp = c->mu_exp;
+  p.inv_Pr = 1.0 / c->Pr;
+  p.bulk_ratio = c->bulk_ratio;
+  p.T_thermo = c->T_thermo;
+  p.inv_T_ref = 1.0 / c->T_ref;
+  p.Pref = c->P_ref / c2;
+  p.kappa_thr = c->kappa_threshold > 0 ? c->kappa_threshold : 1e3;
+  std::memset(&it, 0, sizeof(it));
+  const double* Xin[2] = {c->X_in_lo, c->X_in_hi};
+  const double Tin[2] = {c->T_in_lo, c->T_in_hi}, Pin[2] = {c->P_in_lo, c->P_in_hi};
+  for (int s = 0; s < 2; ++s) {
+    if (!Xin[s] || !(Tin[s] > 0)) continue;
+    double rho = 0.0, inv_m = 0.0, U = 0.0;
+    for (int a = 0; a < M; ++a) {
+      it.rho[s][a] = Pin[s] * Xin[s][a] * p.m[a] / (R_UNIV_SI * Tin[s]);
+      rho += it.rho[s][a];
+    }
+    for (int a = 0; a < M; ++a) {
+      inv_m += (it.rho[s][a] / rho) / p.m[a];
+      U += (it.rho[s][a] / rho) * (p.U0[a] + p.cvR[a] * (Tin[s] - p.T_thermo));
+    }
+    it.rho_sum[s] = rho;
+    it.Rmix[s] = p.RU * inv_m;
+    it.Umix[s] = U;
+    it.T[s] = Tin[s];
+    p.T_in[s] = Tin[s];
+    for (int a = 0; a < M; ++a) p.rho_in[s][a] = it.rho[s][a];
+  }
+}
+
+}  // namespace lbm
+
+extern "C" {
+
+int lbm_create(lbm_ctx** out, const lbm_config* c) {
+  if (!out) return fail(nullptr, LBM_ERR_ARG, "null output pointer");
+  *out = nullptr;
+  int rc = validate(c);
+  if (rc) return rc;
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev < 1) return fail(nullptr, LBM_ERR_CUDA, "no CUDA device");
+
+  lbm_ctx* x = new (std::nothrow) lbm_ctx();
+  if (!x) return fail(nullptr, LBM_ERR_ALLOC, "host allocation failed");
+  x->nx = c->nx; x->ny = c->ny; x->nz = c->nz;
+  x->N = c->nx * c->ny * c->nz;
+  x->D = c->nz > 1 ? 3 : 2;
+  x->Q = x->D == 3 ? 27 : 9;
+  x->M = c->M;
+  x->energy = c->energy ? 1 : 0;
+  x->knudsen = c->knudsen ? 1 : 0;
+  x->L = c->M + 1 + x->energy;
+  x->precision = c->precision;
+  x->S = 0;
+  x->stream = (cudaStream_t)c->stream;
+  x->cur = 0;
+
+  bool ok = (x->precision == LBM_FP64)
+                ? (x->D == 2 ? lbm::get_ops_f64_2d(x->M, x->energy, &x->od) : lbm::get_ops_f64_3d(x->M, x->energy, &x->od))
+                : (x->D == 2 ? lbm::get_ops_f32_2d(x->M, x->energy, &x->of) : lbm::get_ops_f32_3d(x->M, x->energy, &x->of));
+  if (!ok) { delete x; return fail(nullptr, LBM_ERR_ARG, "no kernel for this (M, energy)"); }
+
+  lbm::make_params(c, x->pd, x->itd, x->dt, x->cvel);
+  const int M = x->M;
+  convert_params(x->pd, x->pf);
+  convert_inlet(x->itd, x->itf);
+
+  // ---- device state ---------------------------------------------------------
+  const size_t N = x->N;
+  const size_t rs = real_size(x);
+  const size_t pop_bytes = (size_t)x->L * x->Q * N * rs;
+  void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  size_t sizes[6] = {pop_bytes, pop_bytes, N * rs, N * rs, (size_t)(2 * x->D + M) * N * rs, 64};
+  for (int k = 0; k < 6; ++k) {
+    e = cudaMalloc(&ptrs[k], sizes[k]);
+    if (e != cudaSuccess) {
+      for (int j = 0; j < k; ++j) cudaFree(ptrs[j]);
+      delete x;
+      return fail(nullptr, LBM_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  x->pops[0] = ptrs[0]; x->pops[1] = ptrs[1]; x->phi = ptrs[2]; x->Tfix = ptrs[3]; x->mac = ptrs[4];
+  x->status = (int*)ptrs[5];
+  x->scratch_out = nullptr;
+  x->scratch_bytes = 0;
+
+  // upload static fields in the working precision
+  std::vector<char> hbuf(N * rs);
+  auto upload = [&](void* dst, const double* src) -> cudaError_t {
+    if (rs == 8) std::memcpy(hbuf.data(), src, N * 8);
+    else for (size_t n = 0; n < N; ++n) ((float*)hbuf.data())[n] = (float)src[n];
+    return cudaMemcpy(dst, hbuf.data(), N * rs, cudaMemcpyHostToDevice);
+  };
+  if ((e = upload(x->phi, c->porosity)) != cudaSuccess || (e = upload(x->Tfix, c->T_init)) != cudaSuccess ||
+      (e = cudaMemset(x->status, 0, 64)) != cudaSuccess) {
+    lbm_destroy(x);
+    return cuda_fail(nullptr, e, "upload");
+  }
+  // initial fields -> temporary device copies -> equilibrium populations
+  double *dX = nullptr, *dT = nullptr, *dP = nullptr, *dU = nullptr;
+  size_t nb = N * sizeof(double);
+  e = cudaMalloc(&dX, nb * M);
+  if (e == cudaSuccess) e = cudaMalloc(&dT, nb);
+  if (e == cudaSuccess) e = cudaMalloc(&dP, nb);
+  if (e == cudaSuccess && c->U_init) e = cudaMalloc(&dU, nb * 3);
+  if (e == cudaSuccess) e = cudaMemcpy(dX, c->X_init, nb * M, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dT, c->T_init, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dP, c->P_init, nb, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && c->U_init) e = cudaMemcpy(dU, c->U_init, nb * 3, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    if (x->precision == LBM_FP64)
+      x->od.init(x->pd, dX, dT, dP, dU, x->cvel, R_UNIV_SI, (double*)x->pops[0], (const double*)x->phi, x->stream);
+    else
+      x->of.init(x->pf, dX, dT, dP, dU, x->cvel, R_UNIV_SI, (float*)x->pops[0], (const float*)x->phi, x->stream);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  cudaFree(dX); cudaFree(dT); cudaFree(dP); if (dU) cudaFree(dU);
+  if (e != cudaSuccess) {
+    lbm_destroy(x);
+    return cuda_fail(nullptr, e, "initialisation");
+  }
+  *out = x;
+  return LBM_OK;
+}
+
+static int read_status(lbm_ctx* x) {
+  int st = 0;
+  cudaError_t e = cudaMemcpyAsync(&st, x->status, sizeof(int), cudaMemcpyDeviceToHost, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  if (e != cudaSuccess) return cuda_fail(x, e, "status read");
+  if (st & 1) return fail(x, LBM_ERR_NUMERIC, "non-finite or non-positive density or temperature");
+  return LBM_OK;
+}
+
+}  // extern "C"
+
+// Records a start/stop event pair around one launch when timing is on.
+template <class F>
+static void timed(lbm_ctx* x, int kind, F&& launch) {
+  const size_t kMaxLaunches = 65536;
+  if (!x->timing || x->ev_used >= kMaxLaunches) {
+    launch();
+    return;
+  }
+  if (x->ev.size() < 2 * (x->ev_used + 1)) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
+      if (a) cudaEventDestroy(a);
+      launch();
+      return;
+    }
+    x->ev.push_back(a);
+    x->ev.push_back(b);
+    x->ev_kind.push_back(kind);
+  }
+  x->ev_kind[x->ev_used] = kind;
+  cudaEventRecord(x->ev[2 * x->ev_used], x->stream);
+  launch();
+  cudaEventRecord(x->ev[2 * x->ev_used + 1], x->stream);
+  x->ev_used++;
+}
+
+extern "C" {
+
+int lbm_step(lbm_ctx* x, int n_steps) {
+  if (!x) return LBM_ERR_ARG;
+  if (n_steps < 0) return fail(x, LBM_ERR_ARG, "negative step count");
+  for (int s = 0; s < n_steps; ++s) {
+    if (x->precision == LBM_FP64) {
+      lbm::StepArgs<double> a{(const double*)x->pops[x->cur], (double*)x->pops[1 - x->cur], (const double*)x->phi,
+                              (const double*)x->Tfix, (double*)x->mac, x->status};
+      timed(x, 0, [&] { x->od.macro(x->pd, x->itd, a, x->stream); });
+      timed(x, 1, [&] { x->od.collide(x->pd, x->itd, a, x->stream); });
+    } else {
+      lbm::StepArgs<float> a{(const float*)x->pops[x->cur], (float*)x->pops[1 - x->cur], (const float*)x->phi,
+                             (const float*)x->Tfix, (float*)x->mac, x->status};
+      timed(x, 0, [&] { x->of.macro(x->pf, x->itf, a, x->stream); });
+      timed(x, 1, [&] { x->of.collide(x->pf, x->itf, a, x->stream); });
+    }
+    x->cur = 1 - x->cur;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(x, e, "step launch");
+  return LBM_OK;
+}
+
+int lbm_set_timing(lbm_ctx* x, int enable) {
+  if (!x) return LBM_ERR_ARG;
+  x->timing = enable ? 1 : 0;
+  x->ev_used = 0;
+  return LBM_OK;
+}
+
+int lbm_get_timing(lbm_ctx* x, double* ms, long long* launches) {
+  if (!x || !ms || !launches) return LBM_ERR_ARG;
+  if (!x->timing) return fail(x, LBM_ERR_STATE, "timing is off");
+  cudaError_t e = cudaStreamSynchronize(x->stream);
+  if (e != cudaSuccess) return cuda_fail(x, e, "timing sync");
+  for (int k = 0; k < 3; ++k) { ms[k] = 0.0; launches[k] = 0; }
+  for (size_t i = 0; i < x->ev_used; ++i) {
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, x->ev[2 * i], x->ev[2 * i + 1]);
+    if (e != cudaSuccess) return cuda_fail(x, e, "event time");
+    int k = x->ev_kind[i];
+    ms[k] += t;
+    launches[k] += 1;
+  }
+  return LBM_OK;
+}
+
+int lbm_moments(lbm_ctx* x, int which, void* out, size_t bytes, int out_on_device) {
+  if (!x || !out) return LBM_ERR_ARG;
+  const size_t N = x->N, M = x->M, D = x->D;
+  size_t count;
+  switch (which) {
+    case LBM_MOM_RHO_A: count = M * N; break;
+    case LBM_MOM_J_A: case LBM_MOM_V_A: case LBM_MOM_N_A: count = M * D * N; break;
+    case LBM_MOM_RHO: case LBM_MOM_T: case LBM_MOM_P: case LBM_MOM_RHO_S: count = N; break;
+    case LBM_MOM_U: count = D * N; break;
+    case LBM_MOM_XS: count = (size_t)x->S * N; break;
+    default: return fail(x, LBM_ERR_ARG, "unknown moment selector");
+  }
+  const size_t need = count * sizeof(double);
+  if (bytes < need) return fail(x, LBM_ERR_ARG, "output buffer too small");
+  if (count == 0) return LBM_OK;
+  double* dout = (double*)out;
+  cudaError_t e;
+  if (!out_on_device) {
+    if (x->scratch_bytes < need) {
+      if (x->scratch_out) cudaFree(x->scratch_out);
+      x->scratch_out = nullptr;
+      x->scratch_bytes = 0;
+      e = cudaMalloc(&x->scratch_out, need);
+      if (e != cudaSuccess) return fail(x, LBM_ERR_ALLOC, "moment scratch allocation failed");
+      x->scratch_bytes = need;
+    }
+    dout = x->scratch_out;
+  }
+  if (x->precision == LBM_FP64) {
+    lbm::StepArgs<double> a{(const double*)x->pops[x->cur], nullptr, (const double*)x->phi, (const double*)x->Tfix,
+                            (double*)x->mac, x->status};
+    x->od.moments(x->pd, x->itd, a, which, x->cvel, dout, x->stream);
+  } else {
+    lbm::StepArgs<float> a{(const float*)x->pops[x->cur], nullptr, (const float*)x->phi, (const float*)x->Tfix,
+                           (float*)x->mac, x->status};
+    x->of.moments(x->pf, x->itf, a, which, x->cvel, dout, x->stream);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(x, e, "moments launch");
+  if (!out_on_device) {
+    e = cudaMemcpyAsync(out, dout, need, cudaMemcpyDeviceToHost, x->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+    if (e != cudaSuccess) return cuda_fail(x, e, "moments copy");
+  }
+  return LBM_OK;
+}
+
+size_t lbm_population_bytes(const lbm_ctx* x) {
+  return x ? (size_t)x->L * x->Q * x->N * real_size(x) : 0;
+}
+
+int lbm_get_populations(lbm_ctx* x, void* buf, size_t bytes, int on_device) {
+  if (!x || !buf) return LBM_ERR_ARG;
+  if (bytes != lbm_population_bytes(x)) return fail(x, LBM_ERR_ARG, "population buffer size mismatch");
+  cudaError_t e = cudaMemcpyAsync(buf, x->pops[x->cur], bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(x, e, "population copy");
+}
+
+int lbm_set_populations(lbm_ctx* x, const void* buf, size_t bytes, int on_device) {
+  if (!x || !buf) return LBM_ERR_ARG;
+  if (bytes != lbm_population_bytes(x)) return fail(x, LBM_ERR_ARG, "population buffer size mismatch");
+  cudaError_t e = cudaMemcpyAsync(x->pops[x->cur], buf, bytes,
+                                  on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(x, e, "population copy");
+}
+
+int lbm_sync(lbm_ctx* x) {
+  if (!x) return LBM_ERR_ARG;
+  return read_status(x);
+}
+
+int lbm_info(const lbm_ctx* x, double* out5) {
+  if (!x || !out5) return LBM_ERR_ARG;
+  out5[0] = x->dt;
+  out5[1] = x->cvel;
+  out5[2] = x->L;
+  out5[3] = x->Q;
+  out5[4] = x->D;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* x) {
+  if (!x) return;
+  cudaStreamSynchronize(x->stream);
+  void* bufs[7] = {x->pops[0], x->pops[1], x->phi, x->Tfix, x->mac, x->status, x->scratch_out};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  for (cudaEvent_t ev : x->ev) cudaEventDestroy(ev);
+  delete x;
+}
+
+const char* lbm_last_error(const lbm_ctx* x) {
+  return x ? x->err.c_str() : g_create_error.c_str();
+}
+
+}  // extern "C"

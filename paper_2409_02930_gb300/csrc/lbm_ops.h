@@ -1,0 +1,27 @@
+// Launchers of the kernel instantiations, one table per (precision, dimension).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "lbm_device.cuh"
+
+namespace lbm {
+
+template <class R> struct InletTables;
+template <class R> struct StepArgs;
+
+template <class R>
+struct Ops {
+  void (*macro)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, cudaStream_t);
+  void (*collide)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, cudaStream_t);
+  void (*init)(const Params<R>&, const double*, const double*, const double*, const double*, double, double, R*,
+               const R*, cudaStream_t);
+  void (*moments)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, int, double, double*, cudaStream_t);
+};
+
+bool get_ops_f32_2d(int M, int energy, Ops<float>* out);
+bool get_ops_f64_2d(int M, int energy, Ops<double>* out);
+bool get_ops_f32_3d(int M, int energy, Ops<float>* out);
+bool get_ops_f64_3d(int M, int energy, Ops<double>* out);
+
+}  // namespace lbm

@@ -261,3 +261,38 @@ def capillary_batch(n_cases=64, seed=5, ny=4, steps=2000, nmin=128, nmax=4096) -
                              pore_radius=float(rps[c]), steps=steps,
                              name=f"case{c}_{int(lens[c])}x{ny}"))
     return out
+
+
+def _six_species():
+    """H2, H2O, CO, CO2, CH4, N2-like gas (elements H, C, N, O) at 1073.15 K."""
+    names = ["H2", "H2O", "CO", "CO2", "CH4", "N2"]
+    m = np.array([2.0e-3, 18.0e-3, 28.0e-3, 44.0e-3, 16.0e-3, 28.0e-3])
+    inv = 1.0 / m
+    ref = 1.0 / 2.0e-3 + 1.0 / 18.0e-3
+    D = 8.0e-4 * np.sqrt((inv[:, None] + inv[None, :]) / ref)   # kinetic-theory mass scaling
+    np.fill_diagonal(D, 0.0)
+    mu = np.array([2.0e-5, 4.0e-5, 4.3e-5, 4.1e-5, 2.9e-5, 4.2e-5])
+    cv = np.array([2.5, 3.0, 2.5, 3.0, 3.0, 2.5])
+    elements = np.array([[2, 0, 0, 0], [2, 0, 0, 1], [0, 1, 0, 1], [0, 1, 0, 2], [4, 1, 0, 0], [0, 0, 2, 0]])
+    return names, m, D, mu, cv, elements
+
+
+def anode3d(nx=256, ny=128, nz=128, seed_phi=3, seed_X=4, steps=200, dx=0.25e-6, mechanism=None,
+            name=None, bc_lo=BC_INLET, bc_hi=BC_BOUNCEBACK) -> Workload:
+    """3-D porous anode: six gas species at 1073.15 K and 1 atm, porosity a
+    seeded 3-D Gaussian random field (correlation length 16 nodes) clipped to
+    [0.3, 0.6], fuel-rich reservoir at x = 0, bounce-back wall at x = nx-1
+    (the anode/electrolyte interface of Sec. 5.2), periodic in y and z."""
+    _, m, D, mu, cv, _ = _six_species()
+    N = nx * ny * nz
+    T = 1073.15
+    phi = porosity_field((nz, ny, nx), 16.0, seed_phi)
+    X = random_mole_fractions(6, N, seed_X)
+    fuel = np.array([0.55, 0.05, 0.1, 0.05, 0.2, 0.05])
+    return Workload(
+        name=name or f"anode3d_{nx}x{ny}x{nz}", nx=nx, ny=ny, nz=nz, bc_lo=bc_lo, bc_hi=bc_hi,
+        M=6, energy=True, knudsen=True, dx=dx, theta_max=1.0 / 3.0, T_scale=T, T_ref=T, P_ref=ATM,
+        molar_mass=m, D_ref=D, mu_ref=mu, mu_exp=0.7, Pr=0.7, bulk_ratio=1.0, cv_factor=cv,
+        U0=np.zeros(6), T_thermo=0.0, tortuosity=3.0, pore_radius=0.5e-6, porosity=phi, X_init=X,
+        T_init=np.full(N, T), P_init=np.full(N, ATM), X_in_lo=fuel, X_in_hi=fuel,
+        T_in_lo=T, T_in_hi=T, P_in_lo=ATM, P_in_hi=ATM, steps=steps, mechanism=mechanism)

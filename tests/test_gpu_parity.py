@@ -1,0 +1,138 @@
+"""GPU (CUDA library through the C ABI) against the FP64 oracle, element by
+element on the same seeded inputs.
+
+Tolerances: the FP64 path must match the oracle to 1e-12 relative per moment
+field (max |a - b| / max |b| over the field; densities also pointwise) and per
+population; the FP32 path to 1e-5 on densities and fluxes after 1000 steps.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_02930_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+MOMENTS = ["RHO_A", "J_A", "RHO", "U", "T", "P", "V_A", "N_A", "RHO_S"]
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2409_02930_gb300 import lbm
+    lbm.load()
+    return lbm
+
+
+def field_err(a, b):
+    scale = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / scale) if scale > 0 else float(np.max(np.abs(a)))
+
+
+def pointwise_err(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def bounceback_slab(nx=40, ny=24, steps=150):
+    wl = W.slab(nx=nx, ny=ny, steps=steps, name="bounceback_slab")
+    wl.bc_lo = wl.bc_hi = W.BC_BOUNCEBACK
+    return wl
+
+
+def small_3d(steps=30):
+    wl = W.anode3d(nx=14, ny=10, nz=9, steps=steps)
+    return wl
+
+
+def small_3d_m3(steps=30):
+    base = W.slab(nx=12, ny=10, steps=steps)
+    wl = W.slab(nx=12, ny=10, steps=steps, name="slab3d_12x10x6")
+    wl.nz = 6
+    wl.porosity = W.porosity_field((6, 10, 12), 4.0, 11)
+    wl.X_init = W.random_mole_fractions(3, wl.N, 12)
+    wl.T_init = np.full(wl.N, base.T_init[0])
+    wl.P_init = np.full(wl.N, base.P_init[0])
+    return wl
+
+
+CASES = {
+    "capillary_256x4_fp64_2000": lambda: W.capillary(),
+    "slab_64x40_energy": lambda: W.slab(nx=64, ny=40, steps=300),
+    "slab_48x32_inlet": lambda: W.adjoint_slab(nx=48, ny=32, steps=200),
+    "slab_40x24_bounceback": lambda: bounceback_slab(),
+    "slab3d_m3": lambda: small_3d_m3(),
+    "anode3d_m6": lambda: small_3d(),
+}
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp64_matches_oracle(L, case):
+    wl = CASES[case]()
+    o = oracle.Oracle(wl)
+    g = L.Lattice(wl, precision=L.LBM_FP64)
+    assert abs(g.dt / o.dt - 1) < 1e-14
+    # initial populations, computed independently on each side
+    p0o, p0g = o.pops(), g.populations()
+    for l in range(g.L):
+        assert field_err(p0g[l], p0o[l]) < 1e-14
+    o.step(wl.steps)
+    g.step(wl.steps)
+    g.sync()
+    po, pg = o.pops(), g.populations()
+    for l in range(g.L):
+        e = field_err(pg[l], po[l])
+        assert e < 1e-12, (case, "lattice", l, e)
+    for name in MOMENTS:
+        k = getattr(L, "LBM_MOM_" + name)
+        a, b = g.moments(k), o.moments(k)
+        e = field_err(a, b)
+        assert e < 1e-12, (case, name, e)
+        if name in ("RHO_A", "RHO", "RHO_S", "T", "P") and np.all(b > 0):
+            assert pointwise_err(a, b) < 1e-12, (case, name)
+
+
+def test_fp64_step_split_is_associative(L):
+    """n steps in one call equal n calls of one step (no hidden state)."""
+    wl = W.slab(nx=32, ny=16, steps=10)
+    a = L.Lattice(wl, precision=L.LBM_FP64)
+    b = L.Lattice(wl, precision=L.LBM_FP64)
+    a.step(10)
+    for _ in range(10):
+        b.step(1)
+    assert np.array_equal(a.populations(), b.populations())
+
+
+@pytest.mark.parametrize("case", ["slab_64x40_energy", "capillary_256x4_fp64_2000"])
+def test_fp32_matches_oracle(L, case):
+    wl = CASES[case]()
+    n = 1000
+    o = oracle.Oracle(wl)
+    g = L.Lattice(wl, precision=L.LBM_FP32)
+    o.step(n)
+    g.step(n)
+    g.sync()
+    errs = {}
+    for name in ("RHO_A", "RHO", "J_A", "N_A", "U", "T"):
+        k = getattr(L, "LBM_MOM_" + name)
+        errs[name] = field_err(g.moments(k), o.moments(k))
+    assert errs["RHO_A"] < 1e-5 and errs["RHO"] < 1e-5, errs
+    assert errs["J_A"] < 1e-5 and errs["N_A"] < 1e-5, errs
+
+
+def test_set_get_populations_roundtrip(L):
+    wl = W.slab(nx=16, ny=8)
+    g = L.Lattice(wl, precision=L.LBM_FP64)
+    p = g.populations()
+    q = p * 1.0001
+    g.set_populations(q)
+    assert np.array_equal(g.populations(), q)
+
+
+def test_bad_config_is_rejected(L):
+    wl = W.slab(nx=16, ny=8)
+    wl.porosity = wl.porosity.copy()
+    wl.porosity[3] = 1.5
+    with pytest.raises(L.LbmError):
+        L.Lattice(wl)
+    wl = W.capillary(nx=2, ny=2)
+    with pytest.raises(L.LbmError):
+        L.Lattice(wl)

@@ -159,6 +159,8 @@ def run_ours(args, ws, rank, local):
     rbytes = 4 if prec == lbm.LBM_FP32 else 8
     g = lbm.Lattice(wl, precision=prec, stream=__import__("ctypes").c_void_p(stream.cuda_stream))
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    variant = g.autotune(5) if args.variant is None else args.variant
+    g.set_variant(variant)
 
     def one_step_timed():
         flush.zero_()
@@ -258,7 +260,7 @@ def run_ours(args, ws, rank, local):
                        "l2": "flushed (256 MB write) before every timed step"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                         "kernel": "collide" if cnt[0] > 0 else "fused_step",
+                         "kernel": "collide" if cnt[0] > 0 else "fused_step", "variant": variant,
                          "kernel_ms": per_launch_ms, "step_kernels_ms": step_kernel_ms,
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "bytes_per_node": algorithmic_bytes_per_node(wl, rbytes)},
@@ -320,6 +322,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--variant", type=int, default=None, help="kernel form (-1 two-pass, >= 0 fused tile); default: autotune")
     args = ap.parse_args()
     ws, rank, local = dist_init()
     if args.impl == "reference":

@@ -181,6 +181,22 @@ int lbm_info(const lbm_ctx* ctx, double* out5);
 int lbm_set_timing(lbm_ctx* ctx, int enable);
 int lbm_get_timing(lbm_ctx* ctx, double* ms_by_kind /* [3] */, long long* launches_by_kind /* [3] */);
 
+/*
+ * Kernel forms.  Variant -1 is the two-pass form (a macro-field pass writes
+ * u, Pi and Y_a to a device buffer, then the node update reads it); variants
+ * 0 .. lbm_variant_count()-1 are the fused single-kernel step with different
+ * tile shapes (the macro fields of each tile's halo are recomputed into
+ * shared memory).  Every form computes the same step.  New contexts use
+ * variant 0.  lbm_autotune times every form for `steps` steps on the
+ * current state, restores the state, selects the fastest form and writes its
+ * index to *best (may be NULL).  Errors: LBM_ERR_ARG (unknown variant,
+ * steps < 1), LBM_ERR_ALLOC.
+ */
+int lbm_variant_count(const lbm_ctx* ctx);
+int lbm_set_variant(lbm_ctx* ctx, int variant);
+int lbm_get_variant(const lbm_ctx* ctx);
+int lbm_autotune(lbm_ctx* ctx, int steps, int* best);
+
 /* lbm_destroy -- free the context (synchronises its stream first). NULL is a no-op. */
 void lbm_destroy(lbm_ctx* ctx);
 

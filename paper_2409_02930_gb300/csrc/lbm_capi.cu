@@ -46,6 +46,7 @@ struct lbm_ctx {
   std::vector<cudaEvent_t> ev;       // start/stop pairs
   std::vector<int> ev_kind;
   size_t ev_used;
+  int variant;                       // < 0: two-pass form; >= 0: fused tile shape
 };
 
 namespace {
@@ -218,6 +219,7 @@ int lbm_create(lbm_ctx** out, const lbm_config* c) {
   x->S = 0;
   x->stream = (cudaStream_t)c->stream;
   x->cur = 0;
+  x->variant = 0;
 
   bool ok = (x->precision == LBM_FP64)
                 ? (x->D == 2 ? lbm::get_ops_f64_2d(x->M, x->energy, &x->od) : lbm::get_ops_f64_3d(x->M, x->energy, &x->od))
@@ -325,27 +327,99 @@ static void timed(lbm_ctx* x, int kind, F&& launch) {
   x->ev_used++;
 }
 
+// One time step with the context's kernel form: variant < 0 is the two-pass
+// form, variant >= 0 the fused kernel with that tile shape.
+template <class R>
+static int launch_step(lbm_ctx* x, const lbm::Ops<R>& ops, const lbm::Params<R>& p, const lbm::InletTables<R>& it) {
+  lbm::StepArgs<R> a{(const R*)x->pops[x->cur], (R*)x->pops[1 - x->cur], (const R*)x->phi, (const R*)x->Tfix,
+                     (R*)x->mac, x->status};
+  int rc = 0;
+  if (x->variant < 0) {
+    timed(x, 0, [&] { ops.macro(p, it, a, x->stream); });
+    timed(x, 1, [&] { ops.collide(p, it, a, x->stream); });
+  } else {
+    timed(x, 1, [&] { rc = ops.fused(p, it, a, x->variant, x->stream); });
+  }
+  return rc;
+}
+
+static int step_once(lbm_ctx* x) {
+  int rc = (x->precision == LBM_FP64) ? launch_step(x, x->od, x->pd, x->itd) : launch_step(x, x->of, x->pf, x->itf);
+  if (rc < 0) return fail(x, LBM_ERR_CUDA, "fused kernel configuration failed");
+  x->cur = 1 - x->cur;
+  return LBM_OK;
+}
+
 extern "C" {
 
 int lbm_step(lbm_ctx* x, int n_steps) {
   if (!x) return LBM_ERR_ARG;
   if (n_steps < 0) return fail(x, LBM_ERR_ARG, "negative step count");
   for (int s = 0; s < n_steps; ++s) {
-    if (x->precision == LBM_FP64) {
-      lbm::StepArgs<double> a{(const double*)x->pops[x->cur], (double*)x->pops[1 - x->cur], (const double*)x->phi,
-                              (const double*)x->Tfix, (double*)x->mac, x->status};
-      timed(x, 0, [&] { x->od.macro(x->pd, x->itd, a, x->stream); });
-      timed(x, 1, [&] { x->od.collide(x->pd, x->itd, a, x->stream); });
-    } else {
-      lbm::StepArgs<float> a{(const float*)x->pops[x->cur], (float*)x->pops[1 - x->cur], (const float*)x->phi,
-                             (const float*)x->Tfix, (float*)x->mac, x->status};
-      timed(x, 0, [&] { x->of.macro(x->pf, x->itf, a, x->stream); });
-      timed(x, 1, [&] { x->of.collide(x->pf, x->itf, a, x->stream); });
-    }
-    x->cur = 1 - x->cur;
+    int rc = step_once(x);
+    if (rc) return rc;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(x, e, "step launch");
+  return LBM_OK;
+}
+
+int lbm_variant_count(const lbm_ctx* x) {
+  if (!x) return LBM_ERR_ARG;
+  return x->precision == LBM_FP64 ? x->od.n_variants : x->of.n_variants;
+}
+
+int lbm_set_variant(lbm_ctx* x, int variant) {
+  if (!x) return LBM_ERR_ARG;
+  if (variant < -1 || variant >= lbm_variant_count(x)) return fail(x, LBM_ERR_ARG, "unknown kernel variant");
+  x->variant = variant;
+  return LBM_OK;
+}
+
+int lbm_get_variant(const lbm_ctx* x) { return x ? x->variant : LBM_ERR_ARG; }
+
+int lbm_autotune(lbm_ctx* x, int steps, int* best) {
+  if (!x || steps < 1) return LBM_ERR_ARG;
+  const size_t bytes = lbm_population_bytes(x);
+  void* save = nullptr;
+  cudaError_t e = cudaMalloc(&save, bytes);
+  if (e != cudaSuccess) return fail(x, LBM_ERR_ALLOC, "autotune scratch allocation failed");
+  e = cudaMemcpyAsync(save, x->pops[x->cur], bytes, cudaMemcpyDeviceToDevice, x->stream);
+  const int cur0 = x->cur, var0 = x->variant;
+  const int timing0 = x->timing;
+  x->timing = 0;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&t0);
+  if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  float best_ms = 1e30f;
+  int best_v = var0;
+  const int nv = lbm_variant_count(x);
+  for (int v = -1; v < nv && e == cudaSuccess; ++v) {
+    x->variant = v;
+    if (step_once(x) != LBM_OK) continue;           // warm-up (also configures the kernel)
+    cudaEventRecord(t0, x->stream);
+    int rc = 0;
+    for (int s = 0; s < steps && rc == 0; ++s) rc = step_once(x);
+    cudaEventRecord(t1, x->stream);
+    e = cudaEventSynchronize(t1);
+    float ms = 0.f;
+    if (rc == 0 && e == cudaSuccess && cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess && ms < best_ms) {
+      best_ms = ms;
+      best_v = v;
+    }
+    e = cudaGetLastError();
+  }
+  // restore the state and keep the fastest form
+  x->cur = cur0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(x->pops[x->cur], save, bytes, cudaMemcpyDeviceToDevice, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  cudaFree(save);
+  if (t0) cudaEventDestroy(t0);
+  if (t1) cudaEventDestroy(t1);
+  x->timing = timing0;
+  x->variant = best_v;
+  if (best) *best = best_v;
+  if (e != cudaSuccess) return cuda_fail(x, e, "autotune");
   return LBM_OK;
 }
 

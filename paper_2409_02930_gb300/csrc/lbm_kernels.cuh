@@ -113,6 +113,7 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
                                                   const Grad<R, D, M, EN>& gr, R* __restrict__ dst, int n,
                                                   int* status) {
   constexpr int Q = Lat<D>::Q;
+  constexpr int REST = (Q - 1) / 2;   // index of c = 0
   const int N = p.N;
   if (!(s.rho_s > R(0)) || !(s.rho_f > R(0)) || !finite_<R>(s.T)) flag(status, 1);
 
@@ -141,8 +142,14 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
       psi3<R>(R(0), RaT, K[a]);                                      // eq:fKnudsen
       pr[a] = phi * s.rho_a[a];
     }
+    // The rest population is written last as the remainder of the streamed
+    // zeroth moment, so that rounding cannot bias the conserved masses.
+    R acc[M];
+#pragma unroll
+    for (int a = 0; a < M; ++a) acc[a] = R(0);
     Unroll<0, Q>::run([&](auto ic) {
       constexpr int I = decltype(ic)::value;
+      if (I == REST) return;
       R feq[M], fst[M], fk[M];
 #pragma unroll
       for (int a = 0; a < M; ++a) {
@@ -166,9 +173,13 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
           if (b != a) F += tr.inv_tau_ab[a][b] * (feq[b] - fst[b]);
         F = s.Y[a] * F + tr.inv_tauk[a] * (fst[a] - fk[a]);
         R f = pl.template get<I>(a);
-        dst[(size_t)(a * Q + I) * N + n] = f + R(2) * tr.beta[a] * (feq[a] - f) + (tr.beta[a] - R(1)) * F;
+        R out = f + R(2) * tr.beta[a] * (feq[a] - f) + (tr.beta[a] - R(1)) * F;
+        acc[a] += out;
+        dst[(size_t)(a * Q + I) * N + n] = out;
       }
     });
+#pragma unroll
+    for (int a = 0; a < M; ++a) dst[(size_t)(a * Q + REST) * N + n] = mo.sa[a] - acc[a];
   }
 
   // ---- transport of the mixture (eq:mu, eq:lambda) --------------------------
@@ -198,14 +209,19 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
       psi3<R>(uex * inv_phi, Pex, FX[b]);
     }
     const R pref = phi * s.rho_f;
+    R acc = R(0);
     Unroll<0, Q>::run([&](auto ic) {
       constexpr int I = decltype(ic)::value;
+      if (I == REST) return;
       R fex = pref;
 #pragma unroll
       for (int b = 0; b < D; ++b) fex *= FX[b][c_of<D>(I, b) + 1];
       R f = pl.template get<I>(M);
-      dst[(size_t)(M * Q + I) * N + n] = f + omega * (fex - f);
+      R out = f + omega * (fex - f);
+      acc += out;
+      dst[(size_t)(M * Q + I) * N + n] = out;
     });
+    dst[(size_t)(M * Q + REST) * N + n] = mo.sf - acc;
   }
 
   // ---- energy lattice (eqn:g with eq:gstar, multiplied through by omega - omega1)
@@ -248,8 +264,10 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
               R(0.5) * (R(2) - omega1) * s.P * phi * sdY + s.u[b] * omega * bulk * gr.divu * inv_phi -
               R(0.5) * (omega - omega1) * w[b] * gr.dPi[b];
     }
+    R acc = R(0);
     Unroll<0, Q>::run([&](auto ic) {
       constexpr int I = decltype(ic)::value;
+      if (I == REST) return;
       R geq = G.template value<I>();
       R g = pl.template get<I>(M + 1);
       R out = g + omega * (geq - g);
@@ -258,8 +276,10 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
         for (int b = 0; b < D; ++b)
           if (c_of<D>(I, b) != 0) out += R(0.5) * R(c_of<D>(I, b)) * Dq[b];
       }
+      acc += out;
       dst[(size_t)((M + 1) * Q + I) * N + n] = out;
     });
+    dst[(size_t)((M + 1) * Q + REST) * N + n] = mo.sg - acc;
   }
 }
 

@@ -12,8 +12,12 @@ template <class R> struct StepArgs;
 
 template <class R>
 struct Ops {
+  // two-pass form: macro-field pass, then node update reading it
   void (*macro)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, cudaStream_t);
   void (*collide)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, cudaStream_t);
+  // fused single-kernel step with tile shape `variant` in [0, n_variants); returns < 0 on failure
+  int (*fused)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, int variant, cudaStream_t);
+  int n_variants;
   void (*init)(const Params<R>&, const double*, const double*, const double*, const double*, double, double, R*,
                const R*, cudaStream_t);
   void (*moments)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, int, double, double*, cudaStream_t);

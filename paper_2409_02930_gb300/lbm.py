@@ -83,6 +83,14 @@ def load(path: str = LIB_PATH):
     L.lbm_destroy.restype = None
     L.lbm_last_error.argtypes = [vp]
     L.lbm_last_error.restype = ctypes.c_char_p
+    L.lbm_variant_count.argtypes = [vp]
+    L.lbm_variant_count.restype = ctypes.c_int
+    L.lbm_set_variant.argtypes = [vp, ctypes.c_int]
+    L.lbm_set_variant.restype = ctypes.c_int
+    L.lbm_get_variant.argtypes = [vp]
+    L.lbm_get_variant.restype = ctypes.c_int
+    L.lbm_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
+    L.lbm_autotune.restype = ctypes.c_int
     L.lbm_set_timing.argtypes = [vp, ctypes.c_int]
     L.lbm_set_timing.restype = ctypes.c_int
     L.lbm_get_timing.argtypes = [vp, _dp, ctypes.POINTER(ctypes.c_longlong)]
@@ -204,6 +212,21 @@ class Lattice:
         self._check(load().lbm_moments(self._h, which, ctypes.c_void_p(out.data_ptr()),
                                        out.numel() * out.element_size(), 1), "lbm_moments")
         return out
+
+    def variant_count(self) -> int:
+        return int(load().lbm_variant_count(self._h))
+
+    def set_variant(self, v: int):
+        """-1: two-pass form; 0..variant_count()-1: fused kernel tile shapes."""
+        self._check(load().lbm_set_variant(self._h, int(v)), "lbm_set_variant")
+
+    def variant(self) -> int:
+        return int(load().lbm_get_variant(self._h))
+
+    def autotune(self, steps: int = 5) -> int:
+        best = ctypes.c_int(0)
+        self._check(load().lbm_autotune(self._h, int(steps), ctypes.byref(best)), "lbm_autotune")
+        return best.value
 
     def population_bytes(self) -> int:
         return int(load().lbm_population_bytes(self._h))

@@ -197,6 +197,40 @@ int lbm_set_variant(lbm_ctx* ctx, int variant);
 int lbm_get_variant(const lbm_ctx* ctx);
 int lbm_autotune(lbm_ctx* ctx, int steps, int* best);
 
+/*
+ * lbm_step_noalloc -- one time step that allocates nothing.  The paper has
+ * no counterpart: this entry point exists for callers that cannot allocate
+ * device memory while they run, such as a host framework that owns all
+ * device memory through its own pool allocator, or a time-critical loop in
+ * which cudaMalloc / cudaFree would synchronise the device.
+ *
+ * The caller owns the state: pops_in and pops_out are distinct device
+ * buffers of L*Q*N values ([lattice][i][n], the layout of
+ * lbm_get_populations, the precision of cfg->precision), porosity and
+ * T_fixed are device arrays of N values in that precision (T_fixed is the
+ * temperature of isothermal lattices and is not read when cfg->energy is
+ * on).  cfg supplies the physical parameters (its host arrays molar_mass,
+ * D_ref, mu_ref, cv_factor, U0 and the reservoir fields are read; porosity,
+ * X_init, T_init, P_init are not) and the stream.  The step is the two-pass
+ * form on a D2Q9 lattice (nz == 1, M = 2 or 3, no surface mechanism) and is
+ * issued asynchronously on cfg->stream.
+ *
+ * Its scratch (the macro fields of the first pass and a status word) lives
+ * in one fixed array compiled into the library, lbm_noalloc_scratch_limit()
+ * bytes of macro fields: (4 + M) * N * (8 or 4) bytes must fit, otherwise the
+ * call returns LBM_ERR_ARG.  Every GPU that loads the library holds this
+ * array until the process exits.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  All calls share the array
+ * and it keeps the last call's contents, so calls whose work overlaps on the
+ * GPU race.  The status word is cleared at every call and is not reported.
+ * Errors: LBM_ERR_ARG (invalid arguments, unsupported shape, too large),
+ * LBM_ERR_CUDA (address look-up or launch failed).
+ */
+int lbm_step_noalloc(const lbm_config* cfg, const void* pops_in, void* pops_out, const void* porosity,
+                     const void* T_fixed);
+size_t lbm_noalloc_scratch_limit(void);
+
 /* lbm_destroy -- free the context (synchronises its stream first). NULL is a no-op. */
 void lbm_destroy(lbm_ctx* ctx);
 

@@ -91,6 +91,10 @@ def load(path: str = LIB_PATH):
     L.lbm_get_variant.restype = ctypes.c_int
     L.lbm_autotune.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
     L.lbm_autotune.restype = ctypes.c_int
+    L.lbm_step_noalloc.argtypes = [ctypes.POINTER(LbmConfig), vp, vp, vp, vp]
+    L.lbm_step_noalloc.restype = ctypes.c_int
+    L.lbm_noalloc_scratch_limit.argtypes = []
+    L.lbm_noalloc_scratch_limit.restype = ctypes.c_size_t
     L.lbm_set_timing.argtypes = [vp, ctypes.c_int]
     L.lbm_set_timing.restype = ctypes.c_int
     L.lbm_get_timing.argtypes = [vp, _dp, ctypes.POINTER(ctypes.c_longlong)]
@@ -163,6 +167,20 @@ def make_config(wl, precision: int = LBM_FP64, stream=None, kappa_threshold: flo
         c.Xs_init = arr(mech.Xs_init)
     c.stream = stream if stream is not None else _current_stream()
     return c, keep
+
+
+def step_noalloc(wl, pops_in_ptr: int, pops_out_ptr: int, porosity_ptr: int, t_fixed_ptr: int,
+                 precision: int = LBM_FP64, stream=None) -> int:
+    """One time step through ``lbm_step_noalloc``: for callers that cannot
+    allocate device memory while they run (their framework owns all device
+    memory, or a cudaMalloc would stall a time-critical loop).  The caller
+    passes device pointers to its own state; the library's fixed scratch
+    array is used for the macro fields.  Returns the C status code."""
+    cfg, keep = make_config(wl, precision, stream)
+    rc = load().lbm_step_noalloc(ctypes.byref(cfg), ctypes.c_void_p(pops_in_ptr), ctypes.c_void_p(pops_out_ptr),
+                                 ctypes.c_void_p(porosity_ptr), ctypes.c_void_p(t_fixed_ptr))
+    del keep
+    return int(rc)
 
 
 class Lattice:

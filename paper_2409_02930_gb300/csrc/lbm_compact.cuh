@@ -126,10 +126,24 @@ LBM_HD void ghost_velocity(const Params<R>& p, const R* __restrict__ src, const 
   gh.phi = phiA[x + p.nx * (y + p.ny * z)];
 }
 
-// Moments of the streamed populations (runtime loop form).
-template <class R, int D, int M, bool EN, bool FULL>
-LBM_HD void moments_rt(const Params<R>& p, const InletTables<R>& it, const R* __restrict__ src, const Site<R, D>& st,
-                       const Ghost<R, D>& gh, Moments<R, D, M, EN, FULL>& mo) {
+// Streamed values from global memory with the boundary rules: the handle of
+// a direction is its resolved source (see Site::source).
+template <class R, int D, int M, bool EN>
+struct GlobalPull {
+  const Params<R>& p;
+  const InletTables<R>& it;
+  const R* __restrict__ src;
+  const Site<R, D>& st;
+  const Ghost<R, D>& gh;
+  LBM_HD int prep(int cx, int cy, int cz) const { return st.source(cx, cy, cz); }
+  LBM_HD R get(int h, int l, int i, int cx, int cy, int cz) const {
+    return pull_rt<R, D, M, EN>(p, it, src, gh, st.n, h, l, i, cx, cy, cz);
+  }
+};
+
+// Moments of the streamed populations (runtime loop form), from any puller.
+template <class R, int D, int M, bool EN, bool FULL, class PullF>
+LBM_HD void moments_gen(const PullF& pf, Moments<R, D, M, EN, FULL>& mo) {
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     mo.sa[a] = R(0);
@@ -146,18 +160,18 @@ LBM_HD void moments_rt(const Params<R>& p, const InletTables<R>& it, const R* __
     for (int c = 0; c < D; ++c) mo.Pt[b][c] = R(0);
   }
   for_each_dir<D>([&](int i, int cx, int cy, int cz) {
-    const int s = st.source(cx, cy, cz);
+    const int h = pf.prep(cx, cy, cz);
     const int cc[3] = {cx, cy, cz};
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      R f = pull_rt<R, D, M, EN>(p, it, src, gh, st.n, s, a, i, cx, cy, cz);
+      R f = pf.get(h, a, i, cx, cy, cz);
       mo.sa[a] += f;
       if (FULL) {
 #pragma unroll
         for (int b = 0; b < D; ++b) mo.ja[a][b] += R(cc[b]) * f;
       }
     }
-    R f = pull_rt<R, D, M, EN>(p, it, src, gh, st.n, s, M, i, cx, cy, cz);
+    R f = pf.get(h, M, i, cx, cy, cz);
     mo.sf += f;
 #pragma unroll
     for (int b = 0; b < D; ++b) {
@@ -168,7 +182,7 @@ LBM_HD void moments_rt(const Params<R>& p, const InletTables<R>& it, const R* __
       }
     }
     if (EN) {
-      R g = pull_rt<R, D, M, EN>(p, it, src, gh, st.n, s, M + 1, i, cx, cy, cz);
+      R g = pf.get(h, M + 1, i, cx, cy, cz);
       mo.sg += g;
       if (FULL) {
 #pragma unroll
@@ -178,15 +192,20 @@ LBM_HD void moments_rt(const Params<R>& p, const InletTables<R>& it, const R* __
   });
 }
 
+template <class R, int D, int M, bool EN, bool FULL>
+LBM_HD void moments_rt(const Params<R>& p, const InletTables<R>& it, const R* __restrict__ src, const Site<R, D>& st,
+                       const Ghost<R, D>& gh, Moments<R, D, M, EN, FULL>& mo) {
+  GlobalPull<R, D, M, EN> pf{p, it, src, st, gh};
+  moments_gen<R, D, M, EN, FULL>(pf, mo);
+}
+
 // Collision and store of one node (runtime loop form of collide_and_store).
-template <class R, int D, int M, bool EN>
-LBM_HD void collide_rt(const Params<R>& p, const InletTables<R>& it, const R* __restrict__ src, const Site<R, D>& st,
-                       const Ghost<R, D>& gh, const Moments<R, D, M, EN, true>& mo, const State<R, D, M>& s,
-                       const Grad<R, D, M, EN>& gr, R* __restrict__ dst, int* status) {
+template <class R, int D, int M, bool EN, class PullF>
+LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moments<R, D, M, EN, true>& mo,
+                        const State<R, D, M>& s, const Grad<R, D, M, EN>& gr, R* __restrict__ dst, int* status) {
   constexpr int Q = Lat<D>::Q;
   constexpr int REST = (Q - 1) / 2;
   const size_t N = p.N;
-  const int n = st.n;
   if (!(s.rho_s > R(0)) || !(s.rho_f > R(0)) || !finite_<R>(s.T)) flag(status, 1);
 
   Transport<R, D, M> tr;
@@ -287,7 +306,7 @@ LBM_HD void collide_rt(const Params<R>& p, const InletTables<R>& it, const R* __
   for (int l = 0; l < M + 2; ++l) acc[l] = R(0);
   for_each_dir<D>([&](int i, int cx, int cy, int cz) {
     if (i == REST) return;
-    const int sidx = st.source(cx, cy, cz);
+    const int h = pf.prep(cx, cy, cz);
     // species (eqn:finalNumericalEquationsReactive, eqn:fStar)
     R feq[M], fst[M], fk[M];
 #pragma unroll
@@ -314,7 +333,7 @@ LBM_HD void collide_rt(const Params<R>& p, const InletTables<R>& it, const R* __
       for (int b = 0; b < M; ++b)
         if (b != a) F += tr.inv_tau_ab[a][b] * (feq[b] - fst[b]);
       F = s.Y[a] * F + tr.inv_tauk[a] * (fst[a] - fk[a]);
-      R f = pull_rt<R, D, M, EN>(p, it, src, gh, n, sidx, a, i, cx, cy, cz);
+      R f = pf.get(h, a, i, cx, cy, cz);
       R out = f + R(2) * tr.beta[a] * (feq[a] - f) + (tr.beta[a] - R(1)) * F;
       acc[a] += out;
       dst[(size_t)(a * Q + i) * N + n] = out;
@@ -324,7 +343,7 @@ LBM_HD void collide_rt(const Params<R>& p, const InletTables<R>& it, const R* __
       R fex = pref_f * FX[0][cx + 1];
       if (D >= 2) fex *= sel3(FX[1], cy);
       if (D == 3) fex *= sel3(FX[D - 1], cz);
-      R f = pull_rt<R, D, M, EN>(p, it, src, gh, n, sidx, M, i, cx, cy, cz);
+      R f = pf.get(h, M, i, cx, cy, cz);
       R out = f + omega * (fex - f);
       acc[M] += out;
       dst[(size_t)(M * Q + i) * N + n] = out;
@@ -344,7 +363,7 @@ LBM_HD void collide_rt(const Params<R>& p, const InletTables<R>& it, const R* __
         s2 += t;
       }
       R geq = G.pref_U * prod + G.pref * s2;
-      R g = pull_rt<R, D, M, EN>(p, it, src, gh, n, sidx, M + 1, i, cx, cy, cz);
+      R g = pf.get(h, M + 1, i, cx, cy, cz);
       R out = g + omega * (geq - g);
       const int c2 = cx * cx + cy * cy + cz * cz;
       if (c2 == 1) {
@@ -362,6 +381,14 @@ LBM_HD void collide_rt(const Params<R>& p, const InletTables<R>& it, const R* __
   for (int a = 0; a < M; ++a) dst[(size_t)(a * Q + REST) * N + n] = mo.sa[a] - acc[a];
   dst[(size_t)(M * Q + REST) * N + n] = mo.sf - acc[M];
   if (EN) dst[(size_t)((M + 1) * Q + REST) * N + n] = mo.sg - acc[M + 1];
+}
+
+template <class R, int D, int M, bool EN>
+LBM_HD void collide_rt(const Params<R>& p, const InletTables<R>& it, const R* __restrict__ src, const Site<R, D>& st,
+                       const Ghost<R, D>& gh, const Moments<R, D, M, EN, true>& mo, const State<R, D, M>& s,
+                       const Grad<R, D, M, EN>& gr, R* __restrict__ dst, int* status) {
+  GlobalPull<R, D, M, EN> pf{p, it, src, st, gh};
+  collide_gen<R, D, M, EN>(p, pf, st.n, mo, s, gr, dst, status);
 }
 
 }  // namespace lbm

@@ -2,25 +2,25 @@
 // file defines LBM_REAL, LBM_DIM and LBM_OPS_NAME.
 #include "lbm_fused.cuh"
 #include "lbm_kernels.cuh"
+#include "lbm_march2d.cuh"
 #include "lbm_ops.h"
 
 namespace lbm {
 namespace {
 
-// tile shapes (TX, TY, SEG) of the fused kernel tried by the autotuner
-template <int D> struct Tiles;
-template <> struct Tiles<2> {
-  static constexpr int n = 4;
-  static constexpr int tx[n] = {32, 64, 32, 128};
-  static constexpr int ty[n] = {1, 1, 1, 1};
-  static constexpr int seg[n] = {8, 8, 16, 4};
-};
-template <> struct Tiles<3> {
-  static constexpr int n = 3;
-  static constexpr int tx[n] = {32, 32, 32};
-  static constexpr int ty[n] = {4, 8, 4};
-  static constexpr int seg[n] = {16, 16, 8};
-};
+constexpr size_t kMaxSmem = 227 * 1024;
+
+template <class Kern>
+int configure(Kern kern, size_t smem, bool& done) {
+  if (smem > kMaxSmem) return -1;
+  if (!done) {
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return -1;
+    done = true;
+  }
+  return 0;
+}
 
 template <class R, int D, int M, bool EN>
 struct Launch {
@@ -31,34 +31,58 @@ struct Launch {
   static void collide(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, cudaStream_t s) {
     k_collide<R, D, M, EN><<<grid(p.N), 256, 0, s>>>(p, it, a);
   }
+  // fused step, shared-memory halo ring, tile TX x TY marching SEG planes
   template <int TX, int TY, int SEG>
   static int fused_tile(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, cudaStream_t s) {
     constexpr size_t smem = fused_smem_bytes<R, D, M, EN, TX, TY>();
     auto kern = k_fused<R, D, M, EN, TX, TY, SEG>;
-    static bool configured = false;
-    if (!configured) {
-      if (smem > 48 * 1024 &&
-          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-        return -1;
-      configured = true;
-    }
+    static bool done = false;
+    if (configure(kern, smem, done)) return -1;
     dim3 g((p.nx + TX - 1) / TX, D == 3 ? (p.ny + TY - 1) / TY : (p.ny + SEG - 1) / SEG,
            D == 3 ? (p.nz + SEG - 1) / SEG : 1);
     kern<<<g, TX * TY, smem, s>>>(p, it, a);
     return 0;
   }
-  static int fused(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, int v, cudaStream_t s) {
-    using T = Tiles<D>;
-    switch (v) {
-      case 0: return fused_tile<T::tx[0], T::ty[0], T::seg[0]>(p, it, a, s);
-      case 1: return fused_tile<T::tx[1], T::ty[1], T::seg[1]>(p, it, a, s);
-      case 2: return fused_tile<T::tx[2], T::ty[2], T::seg[2]>(p, it, a, s);
-      case 3:
-        if constexpr (T::n > 3) return fused_tile<T::tx[3 % T::n], T::ty[3 % T::n], T::seg[3 % T::n]>(p, it, a, s);
+  // pipelined 2-D step (cp.async staging), TX columns marching SEG rows
+  template <int TX, int SEG, int MINB>
+  static int march2d(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, cudaStream_t s) {
+    if constexpr (D != 2) {
+      return -1;
+    } else {
+      constexpr size_t smem = march2d_smem_bytes<R, M, EN, TX>();
+      if constexpr (smem > kMaxSmem) {
         return -1;
-      default: return -1;
+      } else {
+        auto kern = k_march2d<R, M, EN, TX, SEG, MINB>;
+        static bool done = false;
+        if (configure(kern, smem, done)) return -1;
+        dim3 g((p.nx + TX - 3) / (TX - 2), (p.ny + SEG - 1) / SEG, 1);
+        kern<<<g, TX, smem, s>>>(p, it, a);
+        return 0;
+      }
     }
   }
+  static int fused(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, int v, cudaStream_t s) {
+    if constexpr (D == 2) {
+      switch (v) {
+        case 0: return march2d<64, 8, 1>(p, it, a, s);
+        case 1: return march2d<64, 8, 6>(p, it, a, s);
+        case 2: return march2d<32, 8, 12>(p, it, a, s);
+        case 3: return march2d<128, 4, 3>(p, it, a, s);
+        case 4: return march2d<64, 16, 6>(p, it, a, s);
+        case 5: return fused_tile<32, 1, 8>(p, it, a, s);
+        default: return -1;
+      }
+    } else {
+      switch (v) {
+        case 0: return fused_tile<32, 4, 16>(p, it, a, s);
+        case 1: return fused_tile<32, 8, 16>(p, it, a, s);
+        case 2: return fused_tile<32, 4, 8>(p, it, a, s);
+        default: return -1;
+      }
+    }
+  }
+  static constexpr int n_variants = (D == 2) ? 6 : 3;
   static void init(const Params<R>& p, const double* X, const double* T, const double* P, const double* U,
                    double cvel, double RU, R* dst, const R* phi, cudaStream_t s) {
     k_init<R, D, M, EN><<<grid(p.N), 256, 0, s>>>(p, X, T, P, U, cvel, RU, dst, phi);
@@ -67,7 +91,7 @@ struct Launch {
                       double* out, cudaStream_t s) {
     k_moments<R, D, M, EN><<<grid(p.N), 256, 0, s>>>(p, it, a, which, cvel, out);
   }
-  static Ops<R> ops() { return Ops<R>{macro, collide, fused, Tiles<D>::n, init, moments}; }
+  static Ops<R> ops() { return Ops<R>{macro, collide, fused, n_variants, init, moments}; }
 };
 
 }  // namespace

@@ -158,14 +158,15 @@ def test_bad_config_is_rejected(L):
 
 @pytest.mark.parametrize("case", ["slab_48x32_inlet", "slab_40x24_bounceback", "anode3d_m6", "slab3d_m3"])
 def test_every_kernel_form_matches_oracle(L, case):
-    """The two-pass form and every fused tile shape match the oracle; the
-    fused shapes share the per-node arithmetic, so they agree bit for bit."""
+    """The two-pass form and every fused kernel form (tile shapes of the
+    pipelined 2-D march and of the shared-memory halo kernel) match the
+    oracle.  The forms sum the gradient stencil in different orders, so they
+    agree with each other to rounding, not bit for bit."""
     wl = CASES[case]()
     steps = 25
     o = oracle.Oracle(wl)
     o.step(steps)
     po = o.pops()
-    ref = None
     g0 = L.Lattice(wl, precision=L.LBM_FP64)
     nv = g0.variant_count()
     g0.close()
@@ -178,11 +179,6 @@ def test_every_kernel_form_matches_oracle(L, case):
         for l in range(g.L):
             e = field_err(pg[l], po[l])
             assert e < 1e-12, (case, v, l, e)
-        if v >= 0:
-            if ref is None:
-                ref = pg
-            else:
-                assert np.array_equal(pg, ref), (case, v)
         g.close()
 
 

@@ -21,6 +21,13 @@ FLAGS = ["-O3", "-std=c++17", "-lineinfo", "--expt-relaxed-constexpr", "-Xcompil
          "-I" + os.path.join(ROOT, "include")]
 
 
+def per_file_flags(src):
+    """The FP32 kernel units use the fast (few-ulp) division, square root and
+    power; their FP32 results are compared with the FP64 oracle at 1e-5.
+    The FP64 units keep IEEE division and square root."""
+    return ["--use_fast_math"] if "_f32_" in os.path.basename(src) else []
+
+
 def sources():
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
@@ -53,7 +60,7 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
         if force or _stale(obj, [src] + hdrs):
-            cmd = [nvcc, "-c", src, "-o", obj] + ARCH + FLAGS + list(extra)
+            cmd = [nvcc, "-c", src, "-o", obj] + ARCH + FLAGS + per_file_flags(src) + list(extra)
             jobs.append(cmd)
 
     def run(cmd):

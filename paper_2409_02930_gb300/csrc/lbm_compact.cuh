@@ -17,8 +17,16 @@ LBM_HD R sel3(const R (&v)[3], int c) {
 
 // Iterate over the discrete velocities: runtime loops over c_z and c_y, the
 // c_x loop unrolled.  f(i, cx, cy, cz).
-template <int D, class F>
+template <int D, bool UNROLL = false, class F>
 LBM_HD void for_each_dir(F&& f) {
+  if constexpr (UNROLL) {
+    // same order, every direction a compile-time constant
+    Unroll<0, Lat<D>::Q>::run([&](auto ic) {
+      constexpr int i = decltype(ic)::value;
+      f(i, c_of<D>(i, 0), c_of<D>(i, 1), c_of<D>(i, 2));
+    });
+    return;
+  }
   const int zlo = (D == 3) ? -1 : 0, zhi = (D == 3) ? 1 : 0;
 #pragma unroll 1
   for (int cz = zlo; cz <= zhi; ++cz) {
@@ -135,6 +143,7 @@ struct GlobalPull {
   const R* __restrict__ src;
   const Site<R, D>& st;
   const Ghost<R, D>& gh;
+  static constexpr bool kUnroll = false;
   LBM_HD int prep(int cx, int cy, int cz) const { return st.source(cx, cy, cz); }
   LBM_HD R get(int h, int l, int i, int cx, int cy, int cz) const {
     return pull_rt<R, D, M, EN>(p, it, src, gh, st.n, h, l, i, cx, cy, cz);
@@ -159,7 +168,7 @@ LBM_HD void moments_gen(const PullF& pf, Moments<R, D, M, EN, FULL>& mo) {
 #pragma unroll
     for (int c = 0; c < D; ++c) mo.Pt[b][c] = R(0);
   }
-  for_each_dir<D>([&](int i, int cx, int cy, int cz) {
+  for_each_dir<D, PullF::kUnroll>([&](int i, int cx, int cy, int cz) {
     const int h = pf.prep(cx, cy, cz);
     const int cc[3] = {cx, cy, cz};
 #pragma unroll
@@ -304,7 +313,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
   R acc[M + 2];
 #pragma unroll
   for (int l = 0; l < M + 2; ++l) acc[l] = R(0);
-  for_each_dir<D>([&](int i, int cx, int cy, int cz) {
+  for_each_dir<D, PullF::kUnroll>([&](int i, int cx, int cy, int cz) {
     if (i == REST) return;
     const int h = pf.prep(cx, cy, cz);
     // species (eqn:finalNumericalEquationsReactive, eqn:fStar)

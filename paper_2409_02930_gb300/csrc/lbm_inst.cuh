@@ -44,16 +44,16 @@ struct Launch {
     return 0;
   }
   // pipelined 2-D step (cp.async staging), TX columns marching SEG rows
-  template <int TX, int SEG, int MINB>
+  template <int TX, int SEG, int MINB, int PD>
   static int march2d(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, cudaStream_t s) {
     if constexpr (D != 2) {
       return -1;
     } else {
-      constexpr size_t smem = march2d_smem_bytes<R, M, EN, TX>();
+      constexpr size_t smem = march2d_smem_bytes<R, M, EN, TX, PD>();
       if constexpr (smem > kMaxSmem) {
         return -1;
       } else {
-        auto kern = k_march2d<R, M, EN, TX, SEG, MINB>;
+        auto kern = k_march2d<R, M, EN, TX, SEG, MINB, PD>;
         static bool done = false;
         if (configure(kern, smem, done)) return -1;
         dim3 g((p.nx + TX - 3) / (TX - 2), (p.ny + SEG - 1) / SEG, 1);
@@ -65,11 +65,11 @@ struct Launch {
   static int fused(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, int v, cudaStream_t s) {
     if constexpr (D == 2) {
       switch (v) {
-        case 0: return march2d<64, 8, 1>(p, it, a, s);
-        case 1: return march2d<64, 8, 6>(p, it, a, s);
-        case 2: return march2d<32, 8, 12>(p, it, a, s);
-        case 3: return march2d<128, 4, 3>(p, it, a, s);
-        case 4: return march2d<64, 16, 6>(p, it, a, s);
+        case 0: return march2d<64, 8, 1, 1>(p, it, a, s);
+        case 1: return march2d<64, 8, 1, 2>(p, it, a, s);
+        case 2: return march2d<32, 8, 1, 1>(p, it, a, s);
+        case 3: return march2d<128, 4, 1, 1>(p, it, a, s);
+        case 4: return march2d<64, 16, 1, 1>(p, it, a, s);
         case 5: return fused_tile<32, 1, 8>(p, it, a, s);
         default: return -1;
       }

@@ -34,21 +34,23 @@ template <class R, int D>
 struct SmemPull {
   const R* col;
   int stride;
+  static constexpr bool kUnroll = (D == 2);
   LBM_HD int prep(int, int, int) const { return 0; }
   LBM_HD R get(int, int l, int i, int, int, int) const { return col[(l * Lat<D>::Q + i) * stride]; }
 };
 
-template <class R, int M, bool EN, int TX>
+// PD rows are prefetched ahead; PD + 2 row buffers are in use at a time
+template <class R, int M, bool EN, int TX, int PD>
 constexpr size_t march2d_smem_bytes() {
-  return sizeof(R) * (size_t)TX * (4 * (M + 1 + (EN ? 1 : 0)) * 9 + 3 * (4 + (EN ? M : 0)));
+  return sizeof(R) * (size_t)TX * ((PD + 2) * (M + 1 + (EN ? 1 : 0)) * 9 + 3 * (4 + (EN ? M : 0)));
 }
 
-template <class R, int M, bool EN, int TX, int SEG, int MINB>
+template <class R, int M, bool EN, int TX, int SEG, int MINB, int PD>
 __global__ void __launch_bounds__(TX, MINB) k_march2d(Params<R> p, InletTables<R> it, StepArgs<R> a) {
   constexpr int D = 2, Q = 9;
   constexpr int NL = M + 1 + (EN ? 1 : 0);
   constexpr int NF = 2 * D + (EN ? M : 0);
-  constexpr int NBUF = 4;
+  constexpr int NBUF = PD + 2;
   extern __shared__ unsigned char smem_raw[];
   R* P = reinterpret_cast<R*>(smem_raw);           // [NBUF][NL*Q][TX]
   R* ring = P + (size_t)NBUF * NL * Q * TX;         // [3][NF][TX]
@@ -99,11 +101,11 @@ __global__ void __launch_bounds__(TX, MINB) k_march2d(Params<R> p, InletTables<R
     cp_async_commit();
   };
 
-  issue(m0 - 1);
-  issue(m0);
+#pragma unroll
+  for (int k = 0; k < PD; ++k) issue(m0 - 1 + k);
 #pragma unroll 1
   for (int s = m0 - 1; s <= mend; ++s) {
-    cp_async_wait<1>();
+    cp_async_wait<PD - 1>();                       // row s has landed
     // ---- gradient inputs of row s (this thread's column) -------------------
     {
       const int y = modp(s, p.ny);
@@ -132,7 +134,7 @@ __global__ void __launch_bounds__(TX, MINB) k_march2d(Params<R> p, InletTables<R
         for (int k = 0; k < M; ++k) rs[(2 * D + k) * TX] = st.Y[k];
       }
     }
-    if (s + 2 <= mend) issue(s + 2);
+    if (s + PD <= mend) issue(s + PD);
     else cp_async_commit();
     __syncthreads();
     // ---- collide row s - 1 ---------------------------------------------------

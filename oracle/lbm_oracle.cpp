@@ -771,13 +771,28 @@ void surface_source(const Oracle& o, const Macro& m, const double* Xs0, double* 
       for (int l = k + 1; l < Rn; ++l) s -= Ab[k * (Rn + 1) + l] * dxi[l];
       dxi[k] = s / Ab[k * (Rn + 1) + k];
     }
+    // positivity-preserving damping: the backward-Euler solution of mass
+    // action keeps every concentration >= 0, so a Newton step that would take
+    // a non-negative concentration below zero is shortened (to 9/10 of the
+    // distance to zero)
+    double alpha = 1.0;
+    for (int a = 0; a < M; ++a) {
+      double d = 0.0;
+      for (int k = 0; k < Rn; ++k) d += scale * o.nu_g[k][a] * dxi[k];
+      if (cg[a] >= 0.0 && cg[a] + d < 0.0) alpha = std::min(alpha, 0.9 * cg[a] / (-d));
+    }
+    for (int s = 0; s < S; ++s) {
+      double d = 0.0;
+      for (int k = 0; k < Rn; ++k) d += o.nu_s[k][s] * dxi[k];
+      if (cs[s] >= 0.0 && cs[s] + d < 0.0) alpha = std::min(alpha, 0.9 * cs[s] / (-d));
+    }
     double dmax = 0.0, xmax = 0.0;
     for (int k = 0; k < Rn; ++k) {
-      xi[k] += dxi[k];
-      dmax = std::max(dmax, std::fabs(dxi[k]));
+      xi[k] += alpha * dxi[k];
+      dmax = std::max(dmax, std::fabs(alpha * dxi[k]));
       xmax = std::max(xmax, std::fabs(xi[k]));
     }
-    if (dmax <= 1e-14 * (xmax + 1e-300)) break;
+    if (alpha == 1.0 && dmax <= 1e-14 * (xmax + 1e-300)) break;
   }
   // gas production per unit volume of porous medium over dt (eq:totalFluidReactionRate,
   // eq:molarToMassRates), converted to kg/m^3 per lattice time step

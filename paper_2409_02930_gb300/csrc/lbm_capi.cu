@@ -12,6 +12,7 @@
 #include "../../include/lbm.h"
 #include "lbm_kernels.cuh"
 #include "lbm_ops.h"
+#include "lbm_surface.cuh"
 
 namespace {
 
@@ -47,6 +48,11 @@ struct lbm_ctx {
   std::vector<int> ev_kind;
   size_t ev_used;
   int variant;                       // < 0: two-pass form; >= 0: fused tile shape
+  // surface mechanism (S > 0): coverages (ping-pong), per-node sources, mechanism table
+  double* Xs[2];
+  int xs_cur;
+  double* rsrc;
+  lbm::MechDev* mech;
 };
 
 namespace {
@@ -127,7 +133,14 @@ int validate(const lbm_config* c) {
         !(c->P_in_hi > 0))
       return fail(nullptr, LBM_ERR_ARG, "inlet faces need reservoir composition, T and P");
   }
-  if (c->S != 0) return fail(nullptr, LBM_ERR_ARG, "surface mechanisms are not supported by this build");
+  if (c->S < 0 || c->S > lbm::SMAX || c->R < 0 || c->R > lbm::RMAX)
+    return fail(nullptr, LBM_ERR_ARG, "surface mechanism too large (S <= 12, R <= 32)");
+  if (c->S > 0) {
+    if (c->R < 1 || !c->nu_gas || !c->nu_surf || !c->A_pre || !c->Ea || !c->surf_cv_factor || !c->surf_U0 ||
+        !c->Xs_init || !(c->gamma > 0) || !(c->a_s > 0))
+      return fail(nullptr, LBM_ERR_ARG, "incomplete surface mechanism");
+    if (!c->energy) return fail(nullptr, LBM_ERR_ARG, "a surface mechanism needs the energy lattice");
+  }
   return LBM_OK;
 }
 
@@ -194,6 +207,62 @@ void make_params(const lbm_config* c, Params<double>& p, InletTables<double>& it
 
 }  // namespace lbm
 
+// Device state of a surface mechanism: coverages, per-node sources and the
+// mechanism table in SI units (the surface source works in FP64).
+static int setup_surface(lbm_ctx* x, const lbm_config* c) {
+  const bool have = (x->precision == LBM_FP64) ? (x->od.react_macro != nullptr) : (x->of.react_macro != nullptr);
+  if (!have) return fail(nullptr, LBM_ERR_ARG, "surface mechanisms need D3Q27 with M = 6 and the energy lattice");
+  const size_t N = x->N;
+  lbm::MechDev h;
+  std::memset(&h, 0, sizeof(h));
+  h.M = c->M;
+  h.S = c->S;
+  h.R = c->R;
+  for (int k = 0; k < c->R; ++k) {
+    int nr = 0;
+    for (int a = 0; a < c->M + c->S; ++a) {
+      const double v = a < c->M ? c->nu_gas[k * c->M + a] : c->nu_surf[k * c->S + (a - c->M)];
+      if (a < c->M) h.nu_g[k][a] = v;
+      else h.nu_s[k][a - c->M] = v;
+      h.nu_all[k][a] = v;
+      if (v < 0) {
+        // mass-action reactant with an integer order
+        const double ord = -v;
+        if (nr >= 4 || ord != (double)(int)ord) return fail(nullptr, LBM_ERR_ARG, "reactant orders must be integers, at most 4 reactants");
+        h.ridx[k][nr] = a;
+        h.rord[k][nr] = (int)ord;
+        ++nr;
+      }
+    }
+    h.nre[k] = nr;
+    h.A[k] = c->A_pre[k];
+    h.Ea[k] = c->Ea[k];
+  }
+  h.gamma = c->gamma;
+  h.a_s = c->a_s;
+  for (int q = 0; q < c->S; ++q) {
+    h.cvs[q] = c->surf_cv_factor[q];
+    h.Us0[q] = c->surf_U0[q];
+  }
+  for (int a = 0; a < c->M; ++a) h.m[a] = c->molar_mass[a];
+  h.T_thermo = c->T_thermo;
+  h.dt = x->dt;
+  h.cvel2 = x->cvel * x->cvel;
+  cudaError_t e = cudaMalloc(&x->mech, sizeof(lbm::MechDev));
+  if (e == cudaSuccess) e = cudaMalloc(&x->Xs[0], (size_t)c->S * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&x->Xs[1], (size_t)c->S * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&x->rsrc, (size_t)(c->M + 1) * N * sizeof(double));
+  if (e != cudaSuccess) return fail(nullptr, LBM_ERR_ALLOC, "surface state allocation failed");
+  std::vector<double> xs((size_t)c->S * N);
+  for (int q = 0; q < c->S; ++q)
+    for (size_t n = 0; n < N; ++n) xs[(size_t)q * N + n] = c->Xs_init[q];
+  e = cudaMemcpy(x->mech, &h, sizeof(h), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(x->Xs[0], xs.data(), xs.size() * sizeof(double), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "surface state upload");
+  x->xs_cur = 0;
+  return LBM_OK;
+}
+
 extern "C" {
 
 int lbm_create(lbm_ctx** out, const lbm_config* c) {
@@ -216,7 +285,7 @@ int lbm_create(lbm_ctx** out, const lbm_config* c) {
   x->knudsen = c->knudsen ? 1 : 0;
   x->L = c->M + 1 + x->energy;
   x->precision = c->precision;
-  x->S = 0;
+  x->S = c->S;
   x->stream = (cudaStream_t)c->stream;
   x->cur = 0;
   x->variant = 0;
@@ -286,6 +355,13 @@ int lbm_create(lbm_ctx** out, const lbm_config* c) {
     lbm_destroy(x);
     return cuda_fail(nullptr, e, "initialisation");
   }
+  if (x->S > 0) {
+    int rc2 = setup_surface(x, c);
+    if (rc2 != LBM_OK) {
+      lbm_destroy(x);
+      return rc2;
+    }
+  }
   *out = x;
   return LBM_OK;
 }
@@ -343,7 +419,26 @@ static int launch_step(lbm_ctx* x, const lbm::Ops<R>& ops, const lbm::Params<R>&
   return rc;
 }
 
+// Reactive step: macro fields and surface source, then the node update with
+// the reaction sources (two-pass form).
+template <class R>
+static void launch_react(lbm_ctx* x, const lbm::Ops<R>& ops, const lbm::Params<R>& p,
+                         const lbm::InletTables<R>& it) {
+  lbm::StepArgs<R> a{(const R*)x->pops[x->cur], (R*)x->pops[1 - x->cur], (const R*)x->phi, (const R*)x->Tfix,
+                     (R*)x->mac, x->status};
+  lbm::ReactArgs ra{x->mech, x->Xs[x->xs_cur], x->Xs[1 - x->xs_cur], x->rsrc};
+  timed(x, 0, [&] { ops.react_macro(p, it, a, ra, x->stream); });
+  timed(x, 1, [&] { ops.react_collide(p, it, a, ra, x->stream); });
+  x->xs_cur = 1 - x->xs_cur;
+}
+
 static int step_once(lbm_ctx* x) {
+  if (x->S > 0) {
+    if (x->precision == LBM_FP64) launch_react(x, x->od, x->pd, x->itd);
+    else launch_react(x, x->of, x->pf, x->itf);
+    x->cur = 1 - x->cur;
+    return LBM_OK;
+  }
   int rc = (x->precision == LBM_FP64) ? launch_step(x, x->od, x->pd, x->itd) : launch_step(x, x->of, x->pf, x->itf);
   if (rc < 0) return fail(x, LBM_ERR_CUDA, "fused kernel configuration failed");
   x->cur = 1 - x->cur;
@@ -456,7 +551,15 @@ int lbm_moments(lbm_ctx* x, int which, void* out, size_t bytes, int out_on_devic
     case LBM_MOM_J_A: case LBM_MOM_V_A: case LBM_MOM_N_A: count = M * D * N; break;
     case LBM_MOM_RHO: case LBM_MOM_T: case LBM_MOM_P: case LBM_MOM_RHO_S: count = N; break;
     case LBM_MOM_U: count = D * N; break;
-    case LBM_MOM_XS: count = (size_t)x->S * N; break;
+    case LBM_MOM_XS: {
+      count = (size_t)x->S * N;
+      if (bytes < count * sizeof(double)) return fail(x, LBM_ERR_ARG, "output buffer too small");
+      if (count == 0) return LBM_OK;
+      cudaError_t e2 = cudaMemcpyAsync(out, x->Xs[x->xs_cur], count * sizeof(double),
+                                       out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, x->stream);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(x->stream);
+      return e2 == cudaSuccess ? LBM_OK : cuda_fail(x, e2, "coverage copy");
+    }
     default: return fail(x, LBM_ERR_ARG, "unknown moment selector");
   }
   const size_t need = count * sizeof(double);
@@ -534,7 +637,8 @@ int lbm_info(const lbm_ctx* x, double* out5) {
 void lbm_destroy(lbm_ctx* x) {
   if (!x) return;
   cudaStreamSynchronize(x->stream);
-  void* bufs[7] = {x->pops[0], x->pops[1], x->phi, x->Tfix, x->mac, x->status, x->scratch_out};
+  void* bufs[11] = {x->pops[0], x->pops[1], x->phi, x->Tfix, x->mac, x->status, x->scratch_out,
+                   x->Xs[0], x->Xs[1], x->rsrc, x->mech};
   for (void* b : bufs)
     if (b) cudaFree(b);
   for (cudaEvent_t ev : x->ev) cudaEventDestroy(ev);

@@ -208,10 +208,23 @@ LBM_HD void moments_rt(const Params<R>& p, const InletTables<R>& it, const R* __
   moments_gen<R, D, M, EN, FULL>(pf, mo);
 }
 
+// Heterogeneous-reaction sources of one node for one step (Sec. 4.2): gas
+// mass production rhodot_a dt per unit volume of porous medium
+// (eq:totalFluidReactionRate) and the change of the fluid internal energy
+// per unit volume (eq:InternalEnergyCell_PC), in lattice energy units.
+template <class R>
+struct NodeSource {
+  R rhodot[MMAX];
+  R dU;
+};
+
 // Collision and store of one node (runtime loop form of collide_and_store).
-template <class R, int D, int M, bool EN, class PullF>
+// With SRC the reaction sources are added: eq:fsourceHetero to the species,
+// eqn:f_source to the momentum lattice and eqn:g_source to the energy lattice.
+template <class R, int D, int M, bool EN, class PullF, bool SRC = false>
 LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moments<R, D, M, EN, true>& mo,
-                        const State<R, D, M>& s, const Grad<R, D, M, EN>& gr, R* __restrict__ dst, int* status) {
+                        const State<R, D, M>& s, const Grad<R, D, M, EN>& gr, R* __restrict__ dst, int* status,
+                        const NodeSource<R>* srcv = nullptr) {
   constexpr int Q = Lat<D>::Q;
   constexpr int REST = (Q - 1) / 2;
   const size_t N = p.N;
@@ -269,9 +282,19 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
     }
   }
   const R pref_f = phi * s.rho_f;
+  // post-collision density (eq:rho_pc) and the eqn:f_source factor
+  R rho_pc = s.rho_f, kpc = R(0);
+  if (SRC) {
+    R sum_rd = R(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a) sum_rd += srcv->rhodot[a];
+    rho_pc = s.rho_f + sum_rd * inv_phi;
+    kpc = rho_pc / s.rho_f - R(1);
+  }
   // energy lattice (eqn:g with eq:gstar, multiplied through by omega - omega1)
-  GeqFactors<R, D> G;
+  GeqFactors<R, D> G, G2;
   R Dq[D];
+  R g_src_total = R(0);
   if (EN) {
     R U = R(0), Ha[M];
 #pragma unroll
@@ -286,6 +309,12 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
 #pragma unroll
     for (int b = 0; b < D; ++b) w2 += w[b] * w[b];
     G.init(phi, s.rho_f, s.u, RT, U);
+    if (SRC) {
+      // source distribution with the post-reaction density and internal energy (eqn:g0mom_source)
+      const R U_pc = (phi * s.rho_f * U + srcv->dU) / (phi * rho_pc);
+      G2.init(phi, rho_pc, s.u, RT, U_pc);
+      g_src_total = phi * rho_pc * (U_pc + R(0.5) * w2) - phi * s.rho_f * (U + R(0.5) * w2);
+    }
 #pragma unroll
     for (int b = 0; b < D; ++b) {
       R qeq = (H + R(0.5) * w2) * s.rho_f * s.u[b];
@@ -344,6 +373,12 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
       F = s.Y[a] * F + tr.inv_tauk[a] * (fst[a] - fk[a]);
       R f = pf.get(h, a, i, cx, cy, cz);
       R out = f + R(2) * tr.beta[a] * (feq[a] - f) + (tr.beta[a] - R(1)) * F;
+      if (SRC) {
+        R shape = E[a][0][cx + 1];
+        if (D >= 2) shape *= sel3(E[a][1], cy);
+        if (D == 3) shape *= sel3(E[a][D - 1], cz);
+        out += srcv->rhodot[a] * shape;                  // eq:fsourceHetero, R^r = fdot^r dt
+      }
       acc[a] += out;
       dst[(size_t)(a * Q + i) * N + n] = out;
     }
@@ -354,6 +389,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
       if (D == 3) fex *= sel3(FX[D - 1], cz);
       R f = pf.get(h, M, i, cx, cy, cz);
       R out = f + omega * (fex - f);
+      if (SRC) out += kpc * fex;                          // eqn:f_source
       acc[M] += out;
       dst[(size_t)(M * Q + i) * N + n] = out;
     }
@@ -374,6 +410,20 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
       R geq = G.pref_U * prod + G.pref * s2;
       R g = pf.get(h, M + 1, i, cx, cy, cz);
       R out = g + omega * (geq - g);
+      if (SRC) {                                          // eqn:g_source
+        R prod2 = R(1), s22 = R(0);
+#pragma unroll
+        for (int b = 0; b < D; ++b) prod2 *= sel3(G2.P1[b], cc[b]);
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          R t2 = sel3(G2.P2[b], cc[b]);
+#pragma unroll
+          for (int a2 = 0; a2 < D; ++a2)
+            if (a2 != b) t2 *= sel3(G2.P1[a2], cc[a2]);
+          s22 += t2;
+        }
+        out += (G2.pref_U * prod2 + G2.pref * s22) - geq;
+      }
       const int c2 = cx * cx + cy * cy + cz * cz;
       if (c2 == 1) {
         R dq = R(0);
@@ -387,9 +437,10 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
   });
   // rest populations as remainders of the streamed zeroth moments
 #pragma unroll
-  for (int a = 0; a < M; ++a) dst[(size_t)(a * Q + REST) * N + n] = mo.sa[a] - acc[a];
-  dst[(size_t)(M * Q + REST) * N + n] = mo.sf - acc[M];
-  if (EN) dst[(size_t)((M + 1) * Q + REST) * N + n] = mo.sg - acc[M + 1];
+  for (int a = 0; a < M; ++a)
+    dst[(size_t)(a * Q + REST) * N + n] = mo.sa[a] + (SRC ? srcv->rhodot[a] : R(0)) - acc[a];
+  dst[(size_t)(M * Q + REST) * N + n] = mo.sf + (SRC ? phi * (rho_pc - s.rho_f) : R(0)) - acc[M];
+  if (EN) dst[(size_t)((M + 1) * Q + REST) * N + n] = mo.sg + g_src_total - acc[M + 1];
 }
 
 template <class R, int D, int M, bool EN>

@@ -4,6 +4,7 @@
 #include "lbm_kernels.cuh"
 #include "lbm_march2d.cuh"
 #include "lbm_ops.h"
+#include "lbm_surface.cuh"
 
 namespace lbm {
 namespace {
@@ -91,7 +92,19 @@ struct Launch {
                       double* out, cudaStream_t s) {
     k_moments<R, D, M, EN><<<grid(p.N), 256, 0, s>>>(p, it, a, which, cvel, out);
   }
-  static Ops<R> ops() { return Ops<R>{macro, collide, fused, n_variants, init, moments}; }
+  static constexpr bool has_react = (D == 3 && M == 6 && EN);
+  static void react_macro(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, const ReactArgs& ra,
+                          cudaStream_t s) {
+    if constexpr (has_react) k_macro_react<R, D, M, EN><<<(p.N + 127) / 128, 128, 0, s>>>(p, it, a, ra);
+  }
+  static void react_collide(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, const ReactArgs& ra,
+                            cudaStream_t s) {
+    if constexpr (has_react) k_collide_react<R, D, M, EN><<<(p.N + 127) / 128, 128, 0, s>>>(p, it, a, ra);
+  }
+  static Ops<R> ops() {
+    return Ops<R>{macro, collide, fused, n_variants, init, moments, has_react ? react_macro : nullptr,
+                  has_react ? react_collide : nullptr};
+  }
 };
 
 }  // namespace

@@ -9,6 +9,7 @@ namespace lbm {
 
 template <class R> struct InletTables;
 template <class R> struct StepArgs;
+struct ReactArgs;
 
 template <class R>
 struct Ops {
@@ -21,6 +22,9 @@ struct Ops {
   void (*init)(const Params<R>&, const double*, const double*, const double*, const double*, double, double, R*,
                const R*, cudaStream_t);
   void (*moments)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, int, double, double*, cudaStream_t);
+  // reactive two-pass form (surface source); null where not instantiated
+  void (*react_macro)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, const ReactArgs&, cudaStream_t);
+  void (*react_collide)(const Params<R>&, const InletTables<R>&, const StepArgs<R>&, const ReactArgs&, cudaStream_t);
 };
 
 bool get_ops_f32_2d(int M, int energy, Ops<float>* out);

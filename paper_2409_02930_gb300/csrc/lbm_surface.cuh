@@ -1,0 +1,216 @@
+// Heterogeneous surface source on the GPU (Sec. 4, Sec. 4.2) and the
+// reactive two-pass step that applies it.
+//
+// Per node and step: mass-action rates with Arrhenius constants, backward
+// Euler in the reaction extents over the physical time step solved by
+// Newton's method (analytic sparse Jacobian, Gaussian elimination with
+// partial pivoting, steps shortened so that no concentration crosses zero).
+// Rates, residual and extents are FP64 whatever the population precision;
+// the Jacobian is FP64 on the FP64 path and FP32 on the FP32 path
+// (iterative refinement to the same FP64 root).  Then the gas mass production
+// (eq:totalFluidReactionRate, eq:molarToMassRates), the new coverages
+// (eq:surfaceMoleFractions, eq:totalSurfaceReactionRate without edges) and
+// the change of the fluid internal energy that keeps the unified internal
+// energy of fluid and adsorbed phases constant (eq:temperatureCell,
+// eq:InternalEnergyCell_PC; no electrochemical work or ohmic heat).
+#pragma once
+
+#include "lbm_compact.cuh"
+
+namespace lbm {
+
+constexpr double R_UNIV_DEV = 8.314462618;    // J/(mol K)
+
+// Mechanism and unit data of a reactive context (device memory, read-only).
+// Species are indexed 0..M-1 (gas, mol/m^3 of fluid) then M..M+S-1 (surface,
+// mol/m^2); reactant lists hold the integer mass-action orders.
+struct MechDev {
+  int M, S, R;
+  double nu_g[RMAX][MMAX];
+  double nu_s[RMAX][SMAX];
+  double nu_all[RMAX][MMAX + SMAX];
+  int nre[RMAX];                     // reactants of each step
+  int ridx[RMAX][4];
+  int rord[RMAX][4];
+  double A[RMAX], Ea[RMAX];
+  double gamma, a_s;
+  double cvs[SMAX], Us0[SMAX];       // molar C_v / R_U and molar U at T_thermo of the adsorbates
+  double m[MMAX];                    // gas molar masses
+  double T_thermo;
+  double dt;                         // physical time step [s]
+  double cvel2;                      // (dx/dt)^2 [m^2/s^2]
+};
+
+__device__ __forceinline__ double ipow(double x, int n) {
+  double r = 1.0;
+  for (int k = 0; k < n; ++k) r *= x;
+  return r;
+}
+
+// Surface source of one node.  rho_a in kg/m^3 of fluid, T in K; returns
+// rhodot[a] (kg/m^3 of porous medium per step), the new coverages and dU
+// (fluid internal energy change per unit volume, lattice units).
+//
+// Mixed precision (iterative refinement): concentrations, rates, the
+// residual F = xi - dt r(xi) and the extents are FP64; the Jacobian of F is
+// assembled and factorised in FP32 (RK = float) or FP64 (RK = double).  The
+// FP64 residual fixes the root, so both converge to the FP64 solution.
+template <int M, class RK>
+__device__ void surface_source_dev(const MechDev& mc, double T, const double* rho_a, double phi, const double* Xs0,
+                                   double* rhodot, double* Xs1, double& dU, int* status) {
+  const int S = mc.S, Rn = mc.R, NS = M + mc.S;
+  double c0[MMAX + SMAX], kr[RMAX], xi[RMAX];
+  for (int a = 0; a < M; ++a) c0[a] = rho_a[a] / mc.m[a];
+  for (int s = 0; s < S; ++s) c0[M + s] = mc.gamma * Xs0[s];
+  for (int k = 0; k < Rn; ++k) {
+    kr[k] = mc.A[k] * exp(-mc.Ea[k] / (R_UNIV_DEV * T));
+    xi[k] = 0.0;
+  }
+  const double scale = mc.a_s / phi;     // gas concentration change per extent
+  RK J[RMAX][RMAX + 1];
+  bool converged = false;
+  for (int it = 0; it < 30; ++it) {
+    double c[MMAX + SMAX], r[RMAX];
+    for (int i = 0; i < NS; ++i) {
+      double d = 0.0;
+      for (int k = 0; k < Rn; ++k) d += mc.nu_all[k][i] * xi[k];
+      c[i] = c0[i] + (i < M ? scale : 1.0) * d;
+    }
+    for (int k = 0; k < Rn; ++k) {
+      double v = kr[k];
+      for (int j = 0; j < mc.nre[k]; ++j) v *= ipow(fmax(c[mc.ridx[k][j]], 0.0), mc.rord[k][j]);
+      r[k] = v;
+    }
+    // J = I - dt dr/dxi: only the reactants of step k enter row k
+    for (int k = 0; k < Rn; ++k) {
+      for (int l = 0; l < Rn; ++l) J[k][l] = (k == l) ? RK(1) : RK(0);
+      for (int j = 0; j < mc.nre[k]; ++j) {
+        const int i = mc.ridx[k][j];
+        if (c[i] > 0.0) {
+          const double g = mc.dt * r[k] * mc.rord[k][j] / c[i] * (i < M ? scale : 1.0);
+          for (int l = 0; l < Rn; ++l) J[k][l] -= RK(g * mc.nu_all[l][i]);
+        }
+      }
+      J[k][Rn] = RK(-(xi[k] - mc.dt * r[k]));
+    }
+    for (int cc = 0; cc < Rn; ++cc) {
+      int pv = cc;
+      for (int k = cc + 1; k < Rn; ++k)
+        if (fabs(J[k][cc]) > fabs(J[pv][cc])) pv = k;
+      if (pv != cc)
+        for (int l = 0; l <= Rn; ++l) {
+          RK t = J[cc][l];
+          J[cc][l] = J[pv][l];
+          J[pv][l] = t;
+        }
+      for (int k = cc + 1; k < Rn; ++k) {
+        RK f = J[k][cc] / J[cc][cc];
+        for (int l = cc; l <= Rn; ++l) J[k][l] -= f * J[cc][l];
+      }
+    }
+    double dxi[RMAX];
+    for (int k = Rn - 1; k >= 0; --k) {
+      RK s2 = J[k][Rn];
+      for (int l = k + 1; l < Rn; ++l) s2 -= J[k][l] * RK(dxi[l]);
+      dxi[k] = (double)(s2 / J[k][k]);
+    }
+    // steps that would take a non-negative concentration below zero are shortened
+    double alpha = 1.0;
+    for (int i = 0; i < NS; ++i) {
+      double d = 0.0;
+      for (int k = 0; k < Rn; ++k) d += mc.nu_all[k][i] * dxi[k];
+      d *= (i < M ? scale : 1.0);
+      if (c[i] >= 0.0 && c[i] + d < 0.0) alpha = fmin(alpha, 0.9 * c[i] / (-d));
+    }
+    double dmax = 0.0, xmax = 0.0;
+    for (int k = 0; k < Rn; ++k) {
+      xi[k] += alpha * dxi[k];
+      dmax = fmax(dmax, fabs(alpha * dxi[k]));
+      xmax = fmax(xmax, fabs(xi[k]));
+    }
+    if (alpha == 1.0 && dmax <= 1e-14 * (xmax + 1e-300)) {
+      converged = true;
+      break;
+    }
+  }
+  if (!converged) flag(status, 4);
+  for (int a = 0; a < M; ++a) {
+    double dn = 0.0;
+    for (int k = 0; k < Rn; ++k) dn += mc.nu_g[k][a] * xi[k];
+    rhodot[a] = mc.a_s * mc.m[a] * dn;
+  }
+  double dUs = 0.0;
+  for (int s = 0; s < S; ++s) {
+    double dn = 0.0;
+    for (int k = 0; k < Rn; ++k) dn += mc.nu_s[k][s] * xi[k];
+    Xs1[s] = Xs0[s] + dn / mc.gamma;
+    const double Us = mc.Us0[s] + mc.cvs[s] * R_UNIV_DEV * (T - mc.T_thermo);
+    dUs += mc.a_s * dn * Us;
+  }
+  dU = -dUs / mc.cvel2;
+}
+
+// Arguments of the reactive passes.
+struct ReactArgs {
+  const MechDev* mech;
+  const double* Xs_in;     // [S][N]
+  double* Xs_out;          // [S][N]
+  double* src;             // [M + 1][N]: rhodot_a, then dU
+};
+
+// Pass 1: macro fields (as k_macro) plus the surface source of the node.
+template <class R, int D, int M, bool EN>
+__global__ void __launch_bounds__(128) k_macro_react(Params<R> p, InletTables<R> it, StepArgs<R> a, ReactArgs ra) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  macro_node<R, D, M, EN>(p, it, a, n);
+  // the surface source needs the streamed species densities and temperature
+  int x, y, z;
+  node_xyz<R, D>(p, n, x, y, z);
+  Site<R, D> st;
+  st.init(p, x, y, z);
+  Ghost<R, D> gh;
+  gh.side = -1;
+  if (st.has_ghost()) ghost_velocity<R, D, M>(p, a.src, a.phi, x, y, z, gh);
+  Moments<R, D, M, EN, false> mo;
+  moments_rt<R, D, M, EN, false>(p, it, a.src, st, gh, mo);
+  State<R, D, M> s;
+  s.template from_moments<EN, false>(p, mo, a.phi[n], EN ? R(0) : a.Tfix[n]);
+  const MechDev& mc = *ra.mech;
+  double rho[MMAX], Xs0[SMAX], Xs1[SMAX], rd[MMAX], dU = 0.0;
+  for (int k = 0; k < M; ++k) rho[k] = (double)s.rho_a[k];
+  for (int k = 0; k < mc.S; ++k) Xs0[k] = ra.Xs_in[(size_t)k * p.N + n];
+  surface_source_dev<M, R>(mc, (double)s.T, rho, (double)s.phi, Xs0, rd, Xs1, dU, a.status);
+  for (int k = 0; k < M; ++k) ra.src[(size_t)k * p.N + n] = rd[k];
+  ra.src[(size_t)M * p.N + n] = dU;
+  for (int k = 0; k < mc.S; ++k) ra.Xs_out[(size_t)k * p.N + n] = Xs1[k];
+}
+
+// Pass 2: node update with the reaction sources.
+template <class R, int D, int M, bool EN>
+__global__ void __launch_bounds__(128) k_collide_react(Params<R> p, InletTables<R> it, StepArgs<R> a, ReactArgs ra) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  int x, y, z;
+  node_xyz<R, D>(p, n, x, y, z);
+  Site<R, D> st;
+  st.init(p, x, y, z);
+  Ghost<R, D> gh;
+  gh.side = -1;
+  if (st.has_ghost()) ghost_velocity<R, D, M>(p, a.src, a.phi, x, y, z, gh);
+  Moments<R, D, M, EN, true> mo;
+  moments_rt<R, D, M, EN, true>(p, it, a.src, st, gh, mo);
+  State<R, D, M> s;
+  s.template from_moments<EN, true>(p, mo, a.phi[n], EN ? R(0) : a.Tfix[n]);
+  Grad<R, D, M, EN> gr;
+  const R* __restrict__ mac = a.mac;
+  const int N = p.N;
+  gr.compute(p, x, y, z, [&](int k, int nb) { return mac[(size_t)k * N + nb]; });
+  NodeSource<R> src;
+  for (int k = 0; k < M; ++k) src.rhodot[k] = (R)ra.src[(size_t)k * N + n];
+  src.dU = (R)ra.src[(size_t)M * N + n];
+  GlobalPull<R, D, M, EN> pf{p, it, a.src, st, gh};
+  collide_gen<R, D, M, EN, GlobalPull<R, D, M, EN>, true>(p, pf, n, mo, s, gr, a.dst, a.status, &src);
+}
+
+}  // namespace lbm

@@ -296,3 +296,82 @@ def anode3d(nx=256, ny=128, nz=128, seed_phi=3, seed_X=4, steps=200, dx=0.25e-6,
         U0=np.zeros(6), T_thermo=0.0, tortuosity=3.0, pore_radius=0.5e-6, porosity=phi, X_init=X,
         T_init=np.full(N, T), P_init=np.full(N, ATM), X_in_lo=fuel, X_in_hi=fuel,
         T_in_lo=T, T_in_hi=T, P_in_lo=ATM, P_in_hi=ATM, steps=steps, mechanism=mechanism)
+
+
+# element order H, C, N, O; atomic masses in kg/mol
+_ATOMIC_MASS = np.array([1.008e-3, 12.011e-3, 14.007e-3, 15.999e-3])
+
+
+def surface_mechanism(seed=4, gamma=2.6e-5, a_s=1.0e7) -> Mechanism:
+    """Seeded mass-action surface mechanism on one catalytic surface for the
+    six-species gas (H2, H2O, CO, CO2, CH4, N2).
+
+    Eight surface species: the empty site s and the adsorbates H(s), O(s),
+    OH(s), H2O(s), CO(s), C(s), CH(s).  Twenty irreversible steps from
+    element- and site-balanced templates (adsorption, dissociative
+    adsorption, desorption, surface exchange; N2 is inert), with
+    log10 A uniform in [5, 15] (SI units of each step's order) and
+    E_a uniform in [50, 150] kJ/mol.  Site density 2.6e-5 mol/m^2 and
+    specific area a_s = 20 / delta_util with delta_util = 2 um (Sec. 5.2).
+    The prefactors are drawn in (mol, cm, s) units and stored in SI."""
+    gas = ["H2", "H2O", "CO", "CO2", "CH4", "N2"]
+    surf = ["s", "H(s)", "O(s)", "OH(s)", "H2O(s)", "CO(s)", "C(s)", "CH(s)"]
+    el_gas = np.array([[2, 0, 0, 0], [2, 0, 0, 1], [0, 1, 0, 1], [0, 1, 0, 2], [4, 1, 0, 0], [0, 0, 2, 0]])
+    el_surf = np.array([[0, 0, 0, 0], [1, 0, 0, 0], [0, 0, 0, 1], [1, 0, 0, 1], [2, 0, 0, 1], [0, 1, 0, 1],
+                        [0, 1, 0, 0], [1, 1, 0, 0]])
+    steps = [
+        ({"H2": -1}, {"s": -2, "H(s)": 2}),
+        ({"H2": 1}, {"H(s)": -2, "s": 2}),
+        ({"H2O": -1}, {"s": -1, "H2O(s)": 1}),
+        ({"H2O": 1}, {"H2O(s)": -1, "s": 1}),
+        ({"CO": -1}, {"s": -1, "CO(s)": 1}),
+        ({"CO": 1}, {"CO(s)": -1, "s": 1}),
+        ({}, {"H(s)": -1, "O(s)": -1, "OH(s)": 1, "s": 1}),
+        ({}, {"OH(s)": -1, "s": -1, "H(s)": 1, "O(s)": 1}),
+        ({}, {"H(s)": -1, "OH(s)": -1, "H2O(s)": 1, "s": 1}),
+        ({}, {"H2O(s)": -1, "s": -1, "H(s)": 1, "OH(s)": 1}),
+        ({"CO2": 1}, {"CO(s)": -1, "O(s)": -1, "s": 2}),
+        ({"CO2": -1}, {"s": -2, "CO(s)": 1, "O(s)": 1}),
+        ({}, {"CO(s)": -1, "s": -1, "C(s)": 1, "O(s)": 1}),
+        ({}, {"C(s)": -1, "O(s)": -1, "CO(s)": 1, "s": 1}),
+        ({"CH4": -1}, {"s": -4, "CH(s)": 1, "H(s)": 3}),
+        ({}, {"CH(s)": -1, "s": -1, "C(s)": 1, "H(s)": 1}),
+        ({}, {"C(s)": -1, "H(s)": -1, "CH(s)": 1, "s": 1}),
+        ({}, {"OH(s)": -2, "H2O(s)": 1, "O(s)": 1}),
+        ({}, {"H2O(s)": -1, "O(s)": -1, "OH(s)": 2}),
+        ({"H2": -1}, {"O(s)": -1, "H2O(s)": 1}),
+    ]
+    R, M, S = len(steps), len(gas), len(surf)
+    nu_g = np.zeros((R, M))
+    nu_s = np.zeros((R, S))
+    for k, (g, s) in enumerate(steps):
+        for name, v in g.items():
+            nu_g[k, gas.index(name)] = v
+        for name, v in s.items():
+            nu_s[k, surf.index(name)] = v
+    # every step conserves elements and sites
+    assert np.all(nu_g @ el_gas + nu_s @ el_surf == 0)
+    assert np.all(nu_s.sum(axis=1) == 0)
+    rng = np.random.default_rng(seed)
+    # log10 A is drawn in the (mol, cm, s) units customary for surface
+    # mechanisms and converted to SI: rate [mol m^-2 s^-1] = 1e4 rate [mol cm^-2 s^-1],
+    # gas concentrations 1e-6 mol cm^-3 per mol m^-3, surface 1e-4 mol cm^-2 per mol m^-2
+    A_cgs = 10.0 ** rng.uniform(5.0, 15.0, R)
+    n_gas = -np.where(nu_g < 0, nu_g, 0).sum(axis=1)
+    n_surf = -np.where(nu_s < 0, nu_s, 0).sum(axis=1)
+    A = A_cgs * 1e4 * 1e-6 ** n_gas * 1e-4 ** n_surf
+    Ea = rng.uniform(50.0e3, 150.0e3, R)
+    ms = el_surf @ _ATOMIC_MASS
+    Xs0 = np.array([0.9, 0.02, 0.02, 0.01, 0.02, 0.02, 0.005, 0.005])
+    # molar C_v / R_U of the adsorbates, molecule-like; the empty site carries
+    # no internal energy, so an adsorbing molecule takes its energy along
+    cvs = np.array([0.0, 1.5, 1.5, 2.5, 3.0, 2.5, 1.5, 2.5])
+    return Mechanism(S=S, R=R, nu_gas=nu_g, nu_surf=nu_s, A=A, Ea=Ea, gamma=gamma, a_s=a_s,
+                     surf_molar_mass=ms, surf_cv_factor=cvs, surf_U0=np.zeros(S),
+                     gas_U0_molar=np.zeros(M), elements_gas=el_gas, elements_surf=el_surf, Xs_init=Xs0)
+
+
+def anode3d_reactive(nx=256, ny=128, nz=128, steps=200, name=None) -> Workload:
+    """The 3-D anode with the seeded surface mechanism."""
+    return anode3d(nx=nx, ny=ny, nz=nz, steps=steps, mechanism=surface_mechanism(),
+                   name=name or f"anode3d_reactive_{nx}x{ny}x{nz}")

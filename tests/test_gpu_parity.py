@@ -190,3 +190,43 @@ def test_autotune_restores_state(L):
     assert -1 <= best < g.variant_count()
     assert g.variant() == best
     assert np.array_equal(g.populations(), p0)
+
+
+def reactive_3d(steps=20, nx=12, ny=8, nz=6):
+    return W.anode3d_reactive(nx=nx, ny=ny, nz=nz, steps=steps, name=f"anode3d_reactive_{nx}x{ny}x{nz}")
+
+
+def test_fp64_reactive_matches_oracle(L):
+    """3-D anode with the seeded surface mechanism (reservoir at x = 0,
+    bounce-back wall at x = nx-1): populations, moments and coverages of the
+    FP64 GPU step match the oracle."""
+    wl = reactive_3d()
+    o = oracle.Oracle(wl)
+    g = L.Lattice(wl, precision=L.LBM_FP64)
+    o.step(wl.steps)
+    g.step(wl.steps)
+    g.sync()
+    po, pg = o.pops(), g.populations()
+    for l in range(g.L):
+        assert field_err(pg[l], po[l]) < 1e-12, ("lattice", l)
+    for name in ("RHO_A", "RHO", "U", "T", "N_A"):
+        k = getattr(L, "LBM_MOM_" + name)
+        assert field_err(g.moments(k), o.moments(k)) < 1e-12, name
+    xs_g, xs_o = g.moments(L.LBM_MOM_XS), o.moments(oracle.MOM_XS)
+    assert np.max(np.abs(xs_g - xs_o)) < 1e-12
+    assert np.max(np.abs(xs_o - wl.mechanism.Xs_init[:, None])) > 1e-8     # the surface did react
+
+
+def test_fp32_reactive_matches_oracle(L):
+    """FP32 populations with the FP64 surface source: densities within 1e-5
+    after 200 steps; coverages (fractions of order one) within 1e-8."""
+    wl = reactive_3d(steps=200)
+    o = oracle.Oracle(wl)
+    g = L.Lattice(wl, precision=L.LBM_FP32)
+    o.step(wl.steps)
+    g.step(wl.steps)
+    g.sync()
+    e = field_err(g.moments(L.LBM_MOM_RHO_A), o.moments(oracle.MOM_RHO_A))
+    assert e < 1e-5, e
+    xs_g, xs_o = g.moments(L.LBM_MOM_XS), o.moments(oracle.MOM_XS)
+    assert np.max(np.abs(xs_g - xs_o)) < 1e-8

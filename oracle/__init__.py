@@ -3,7 +3,10 @@
 Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It compiles ``lbm_oracle.cpp`` (plain
 C++ loops in double precision, OpenMP over nodes) with the host compiler and
-drives it through ctypes.  It shares no code with the CUDA library.
+drives it through ctypes.  It shares no code with the CUDA library.  The same
+source built with -DORACLE_DUAL carries forward-mode dual numbers: exact
+directional derivatives of the time loop with respect to the porosity field,
+pore radius and tortuosity (``Oracle(wl, dual=True)``, ``set_tangents``).
 """
 from __future__ import annotations
 
@@ -18,8 +21,11 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lbm_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblbm_oracle.so")
+_LIB_DUAL = os.path.join(_BUILD, "liblbm_oracle_dual.so")
+LANES = 8            # derivative lanes of the dual-number build
 _lock = threading.Lock()
 _lib = None
+_lib_dual = None
 
 BC_CODE = {"periodic": 0, "inlet": 1, "bounceback": 2}
 
@@ -52,40 +58,62 @@ class OcConfig(ctypes.Structure):
     ]
 
 
+def _compile(out: str, defines, force: bool) -> str:
+    with _lock:
+        if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+            return out
+        os.makedirs(_BUILD, exist_ok=True)
+        tmp = out + f".tmp{os.getpid()}"
+        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared"] + list(defines) + ["-o", tmp, _SRC]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, out)
+        return out
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle shared library (host compiler, -O2, OpenMP)."""
-    with _lock:
-        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
-            return _LIB
-        os.makedirs(_BUILD, exist_ok=True)
-        tmp = _LIB + f".tmp{os.getpid()}"
-        cmd = ["g++", "-O2", "-std=c++17", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC]
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, _LIB)
-        return _LIB
+    return _compile(_LIB, [], force)
+
+
+def build_dual(force: bool = False) -> str:
+    """Compile the forward-mode dual-number build of the same source."""
+    return _compile(_LIB_DUAL, [f"-DORACLE_DUAL={LANES}"], force)
+
+
+def _declare(L):
+    L.oc_create.restype = ctypes.c_void_p
+    L.oc_create.argtypes = [ctypes.POINTER(OcConfig)]
+    L.oc_destroy.argtypes = [ctypes.c_void_p]
+    L.oc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    for fn in ("oc_get_pops", "oc_set_pops", "oc_get_pulled", "oc_info"):
+        getattr(L, fn).argtypes = [ctypes.c_void_p, _dp]
+    L.oc_get_pops_lane.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+    L.oc_get_diag.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+    L.oc_moments.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+    L.oc_moments_lane.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp]
+    L.oc_set_tangents.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+    L.oc_threads.restype = ctypes.c_int
+    L.oc_lanes.restype = ctypes.c_int
+    L.oc_product_form.argtypes = [ctypes.c_int, _dp, _dp, _dp]
+    L.oc_energy_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp,
+                                        ctypes.c_double, ctypes.c_double, _dp]
+    L.oc_qr_solve.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
+    L.oc_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
+    return L
 
 
 def lib():
     global _lib
     if _lib is None:
-        path = build()
-        L = ctypes.CDLL(path)
-        L.oc_create.restype = ctypes.c_void_p
-        L.oc_create.argtypes = [ctypes.POINTER(OcConfig)]
-        L.oc_destroy.argtypes = [ctypes.c_void_p]
-        L.oc_step.argtypes = [ctypes.c_void_p, ctypes.c_int]
-        for fn in ("oc_get_pops", "oc_set_pops", "oc_get_pulled", "oc_info"):
-            getattr(L, fn).argtypes = [ctypes.c_void_p, _dp]
-        L.oc_get_diag.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
-        L.oc_moments.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
-        L.oc_threads.restype = ctypes.c_int
-        L.oc_product_form.argtypes = [ctypes.c_int, _dp, _dp, _dp]
-        L.oc_energy_equilibrium.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_double, _dp,
-                                            ctypes.c_double, ctypes.c_double, _dp]
-        L.oc_qr_solve.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp]
-        L.oc_lattice.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]
-        _lib = L
+        _lib = _declare(ctypes.CDLL(build()))
     return _lib
+
+
+def lib_dual():
+    global _lib_dual
+    if _lib_dual is None:
+        _lib_dual = _declare(ctypes.CDLL(build_dual()))
+    return _lib_dual
 
 
 def _ptr(a: np.ndarray):
@@ -99,8 +127,11 @@ def _f64(a) -> np.ndarray:
 class Oracle:
     """One oracle lattice built from a ``workloads.Workload``."""
 
-    def __init__(self, wl, nthreads: int = 0):
-        L = lib()
+    def __init__(self, wl, nthreads: int = 0, dual: bool = False):
+        """dual=True uses the dual-number build: every quantity carries
+        ``LANES`` directional derivatives, seeded with ``set_tangents``."""
+        L = lib_dual() if dual else lib()
+        self._L = L
         self.wl = wl
         keep = {}
 
@@ -165,42 +196,69 @@ class Oracle:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and _lib is not None:
-            _lib.oc_destroy(h)
+        if h is not None:
+            self._L.oc_destroy(h)
             self._h = None
 
     def step(self, n: int = 1):
-        lib().oc_step(self._h, int(n))
+        self._L.oc_step(self._h, int(n))
 
     def pops(self) -> np.ndarray:
         out = np.empty((self.nl, self.Q, self.N))
-        lib().oc_get_pops(self._h, _ptr(out))
+        self._L.oc_get_pops(self._h, _ptr(out))
         return out
 
     def set_pops(self, p: np.ndarray):
         a = _f64(p).reshape(self.nl, self.Q, self.N)
-        lib().oc_set_pops(self._h, _ptr(a))
+        self._L.oc_set_pops(self._h, _ptr(a))
 
     def pulled(self) -> np.ndarray:
         out = np.empty((self.nl, self.Q, self.N))
-        lib().oc_get_pulled(self._h, _ptr(out))
+        self._L.oc_get_pulled(self._h, _ptr(out))
         return out
 
     def diag(self, which: int) -> np.ndarray:
         shapes = {0: (self.M, 3, self.N), 1: (3, self.N), 2: (self.N,), 3: (self.N,),
                   4: (self.N,), 5: (self.M, self.N)}
         out = np.empty(shapes[which])
-        lib().oc_get_diag(self._h, which, _ptr(out))
+        self._L.oc_get_diag(self._h, which, _ptr(out))
         return out
 
-    def moments(self, which: int) -> np.ndarray:
+    def moments(self, which: int, lane=None) -> np.ndarray:
+        """Field `which`; with `lane` (dual build) its derivative in that lane."""
         M, D, N = self.M, self.D, self.N
         S = self.wl.mechanism.S if self.wl.mechanism is not None else 0
         shapes = {MOM_RHO_A: (M, N), MOM_J_A: (M, D, N), MOM_RHO: (N,), MOM_U: (D, N),
                   MOM_T: (N,), MOM_P: (N,), MOM_V_A: (M, D, N), MOM_N_A: (M, D, N),
                   MOM_XS: (S, N), MOM_RHO_S: (N,)}
         out = np.empty(shapes[which])
-        lib().oc_moments(self._h, which, _ptr(out))
+        if lane is None:
+            self._L.oc_moments(self._h, which, _ptr(out))
+        else:
+            self._L.oc_moments_lane(self._h, which, int(lane), _ptr(out))
+        return out
+
+    # ---- dual-number build: exact directional derivatives ----------------
+    def set_tangents(self, dphi=None, dpore=None, dtort=None):
+        """Seed the derivative lanes: dphi [LANES][N] directions of the
+        porosity field, dpore / dtort [LANES] of the pore radius [m] and the
+        tortuosity.  Resets the state to the initial equilibria."""
+        K = LANES
+
+        def opt(a, shape):
+            if a is None:
+                return None
+            b = np.zeros(shape)
+            a = np.asarray(a, float)
+            b[:a.shape[0]] = a.reshape((a.shape[0],) + shape[1:])
+            return b
+
+        keep = [opt(dphi, (K, self.N)), opt(dpore, (K,)), opt(dtort, (K,))]
+        self._L.oc_set_tangents(self._h, *[_ptr(a) if a is not None else None for a in keep])
+
+    def pops_lane(self, lane: int) -> np.ndarray:
+        out = np.empty((self.nl, self.Q, self.N))
+        self._L.oc_get_pops_lane(self._h, int(lane), _ptr(out))
         return out
 
 

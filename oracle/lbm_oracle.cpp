@@ -25,6 +25,74 @@
 #include <omp.h>
 #endif
 
+// ---------------------------------------------------------------------------
+// Scalar type.  The plain build computes in double.  Built with
+// -DORACLE_DUAL=K every quantity also carries K directional derivatives
+// (forward-mode dual numbers): the value part repeats the plain build's
+// operations one for one and each derivative part applies the chain rule of
+// the operation, so the derivative parts after n steps are exact
+// Jacobian-vector products of the whole time loop with respect to the seeded
+// inputs (porosity field, pore radius, tortuosity).
+// ---------------------------------------------------------------------------
+inline double rmax(double a, double b) { return (a < b) ? b : a; }
+inline double rmin(double a, double b) { return (b < a) ? b : a; }
+#ifndef ORACLE_DUAL
+typedef double real;
+inline double comp(double x, int) { return x; }
+inline double r_sqrt(double x) { return std::sqrt(x); }
+inline double r_exp(double x) { return std::exp(x); }
+inline double r_pow(double x, double p) { return std::pow(x, p); }
+inline double r_fabs(double x) { return std::fabs(x); }
+#else
+const int NT = ORACLE_DUAL;
+struct real {
+  double v;
+  double d[NT];
+  real() : v(0.0) { for (int k = 0; k < NT; ++k) d[k] = 0.0; }
+  real(double x) : v(x) { for (int k = 0; k < NT; ++k) d[k] = 0.0; }
+  real(int x) : real((double)x) {}
+  real& operator+=(const real& b) { v += b.v; for (int k = 0; k < NT; ++k) d[k] += b.d[k]; return *this; }
+  real& operator-=(const real& b) { v -= b.v; for (int k = 0; k < NT; ++k) d[k] -= b.d[k]; return *this; }
+  real& operator*=(const real& b) {            // (uv)' = u'v + uv'
+    for (int k = 0; k < NT; ++k) d[k] = d[k] * b.v + v * b.d[k];
+    v *= b.v;
+    return *this;
+  }
+  real& operator/=(const real& b) {            // (u/v)' = (u' - (u/v) v')/v
+    const double q = v / b.v;
+    for (int k = 0; k < NT; ++k) d[k] = (d[k] - q * b.d[k]) / b.v;
+    v = q;
+    return *this;
+  }
+};
+inline real operator+(real a, const real& b) { return a += b; }
+inline real operator-(real a, const real& b) { return a -= b; }
+inline real operator*(real a, const real& b) { return a *= b; }
+inline real operator/(real a, const real& b) { return a /= b; }
+inline real operator-(const real& a) { real r; r.v = -a.v; for (int k = 0; k < NT; ++k) r.d[k] = -a.d[k]; return r; }
+inline bool operator<(const real& a, const real& b) { return a.v < b.v; }
+inline bool operator>(const real& a, const real& b) { return a.v > b.v; }
+inline bool operator<=(const real& a, const real& b) { return a.v <= b.v; }
+inline bool operator>=(const real& a, const real& b) { return a.v >= b.v; }
+inline bool operator==(const real& a, const real& b) { return a.v == b.v; }
+inline bool operator!=(const real& a, const real& b) { return a.v != b.v; }
+inline double comp(const real& x, int lane) { return lane < 0 ? x.v : x.d[lane]; }
+inline real chain(const real& x, double fx, double dfx) {
+  real r;
+  r.v = fx;
+  for (int k = 0; k < NT; ++k) r.d[k] = dfx * x.d[k];
+  return r;
+}
+inline real r_sqrt(const real& x) { const double s = std::sqrt(x.v); return chain(x, s, 0.5 / s); }
+inline real r_exp(const real& x) { const double e = std::exp(x.v); return chain(x, e, e); }
+inline real r_pow(const real& x, double p) {
+  return chain(x, std::pow(x.v, p), p == 0.0 ? 0.0 : p * std::pow(x.v, p - 1.0));
+}
+inline real r_fabs(const real& x) { return x.v < 0 ? -x : x; }
+inline real rmax(const real& a, const real& b) { return (a < b) ? b : a; }
+inline real rmin(const real& a, const real& b) { return (b < a) ? b : a; }
+#endif
+
 namespace {
 
 const double R_UNIV = 8.314462618;      // J/(mol K)
@@ -62,15 +130,15 @@ Lattice make_lattice(int D) {
 // ---------------------------------------------------------------------------
 // Product form, Sec. 2.2: eqn:phi0, eqn:phiPlus, eqn:phis and eq:prod.
 // ---------------------------------------------------------------------------
-double psi(int c, double xi, double P) {
+real psi(int c, real xi, real P) {
   if (c == 0) return 1.0 - P;
   if (c == 1) return 0.5 * (xi + P);
   return 0.5 * (-xi + P);
 }
 
-void product_form(const Lattice& L, const double* xi, const double* P, double* out) {
+void product_form(const Lattice& L, const real* xi, const real* P, real* out) {
   for (int i = 0; i < L.Q; ++i) {
-    double v = 1.0;
+    real v = 1.0;
     for (int a = 0; a < L.D; ++a) v *= psi(L.c[i][a], xi[a], P[a]);
     out[i] = v;
   }
@@ -90,20 +158,20 @@ double lattice_weight(const Lattice& L, int i) {
 // O_alpha of eqn:oalpha literally (Sec. 3.3).
 // ---------------------------------------------------------------------------
 const int PDEG = 10;
-struct Poly { double a[PDEG + 1]; };
+struct Poly { real a[PDEG + 1]; };
 
 Poly poly_zero() { Poly p; for (int k = 0; k <= PDEG; ++k) p.a[k] = 0.0; return p; }
 
 // O A = RT dA/dw + w A   (eqn:oalpha; reading R4: w = u/phi)
-Poly poly_apply_O(const Poly& A, double RT) {
+Poly poly_apply_O(const Poly& A, real RT) {
   Poly r = poly_zero();
   for (int k = 1; k <= PDEG; ++k) r.a[k - 1] += RT * k * A.a[k];
   for (int k = 0; k < PDEG; ++k) r.a[k + 1] += A.a[k];
   return r;
 }
 
-double poly_eval(const Poly& p, double w) {
-  double s = 0.0;
+real poly_eval(const Poly& p, real w) {
+  real s = 0.0;
   for (int k = PDEG; k >= 0; --k) s = s * w + p.a[k];
   return s;
 }
@@ -111,10 +179,10 @@ double poly_eval(const Poly& p, double w) {
 // Psi_c(O, O^2) applied to the one-axis function h(w), evaluated at w:
 // c = 0: h - O^2 h ; c = +-1: (+-O h + O^2 h)/2  (eqn:phi0..eqn:phis with
 // xi -> O and P -> O^2, as eq:geq_i prescribes).
-double psi_operator(int c, const Poly& h, double RT, double w) {
+real psi_operator(int c, const Poly& h, real RT, real w) {
   Poly o1 = poly_apply_O(h, RT);
   Poly o2 = poly_apply_O(o1, RT);
-  double h0 = poly_eval(h, w), v1 = poly_eval(o1, w), v2 = poly_eval(o2, w);
+  real h0 = poly_eval(h, w), v1 = poly_eval(o1, w), v2 = poly_eval(o2, w);
   if (c == 0) return h0 - v2;
   if (c == 1) return 0.5 * (v1 + v2);
   return 0.5 * (-v1 + v2);
@@ -125,20 +193,20 @@ double psi_operator(int c, const Poly& h, double RT, double w) {
 // w = u/phi (reading R4).  E is a sum of separable terms (a constant and one
 // quadratic per axis); the product of one-axis operators acts on each term
 // axis by axis.
-void energy_equilibrium(const Lattice& L, double phi, double rho, const double* u, double RT,
-                        double U, double* out) {
-  double w[3];
+void energy_equilibrium(const Lattice& L, real phi, real rho, const real* u, real RT,
+                        real U, real* out) {
+  real w[3];
   for (int a = 0; a < L.D; ++a) w[a] = u[a] / phi;
   Poly one = poly_zero(); one.a[0] = 1.0;
   Poly half_w2 = poly_zero(); half_w2.a[2] = 0.5;
   for (int i = 0; i < L.Q; ++i) {
     // term U * 1
-    double t = U;
+    real t = U;
     for (int a = 0; a < L.D; ++a) t *= psi_operator(L.c[i][a], one, RT, w[a]);
-    double s = t;
+    real s = t;
     // terms w_beta^2/2
     for (int b = 0; b < L.D; ++b) {
-      double tb = 1.0;
+      real tb = 1.0;
       for (int a = 0; a < L.D; ++a)
         tb *= psi_operator(L.c[i][a], (a == b) ? half_w2 : one, RT, w[a]);
       s += tb;
@@ -152,31 +220,31 @@ void energy_equilibrium(const Lattice& L, double phi, double rho, const double* 
 // diffusion-velocity system (Sec. 2.3, after eqn:transform1Alternate).
 // A is n x n row-major, b has nrhs columns (b[k*nrhs + r]).
 // ---------------------------------------------------------------------------
-void householder_qr_solve(int n, const double* Ain, int nrhs, const double* bin, double* x) {
-  double A[MMAX * MMAX], B[MMAX * 3];
+void householder_qr_solve(int n, const real* Ain, int nrhs, const real* bin, real* x) {
+  real A[MMAX * MMAX], B[MMAX * 3];
   for (int k = 0; k < n * n; ++k) A[k] = Ain[k];
   for (int k = 0; k < n * nrhs; ++k) B[k] = bin[k];
   for (int j = 0; j < n; ++j) {
-    double norm = 0.0;
+    real norm = 0.0;
     for (int i = j; i < n; ++i) norm += A[i * n + j] * A[i * n + j];
-    norm = std::sqrt(norm);
+    norm = r_sqrt(norm);
     if (norm == 0.0) continue;
-    double alpha = (A[j * n + j] > 0) ? -norm : norm;
-    double v[MMAX];
+    real alpha = (A[j * n + j] > 0) ? -norm : norm;
+    real v[MMAX];
     for (int i = 0; i < n; ++i) v[i] = 0.0;
     for (int i = j; i < n; ++i) v[i] = A[i * n + j];
     v[j] -= alpha;
-    double vv = 0.0;
+    real vv = 0.0;
     for (int i = j; i < n; ++i) vv += v[i] * v[i];
     if (vv == 0.0) continue;
     for (int k = j; k < n; ++k) {
-      double s = 0.0;
+      real s = 0.0;
       for (int i = j; i < n; ++i) s += v[i] * A[i * n + k];
       s = 2.0 * s / vv;
       for (int i = j; i < n; ++i) A[i * n + k] -= s * v[i];
     }
     for (int r = 0; r < nrhs; ++r) {
-      double s = 0.0;
+      real s = 0.0;
       for (int i = j; i < n; ++i) s += v[i] * B[i * nrhs + r];
       s = 2.0 * s / vv;
       for (int i = j; i < n; ++i) B[i * nrhs + r] -= s * v[i];
@@ -184,7 +252,7 @@ void householder_qr_solve(int n, const double* Ain, int nrhs, const double* bin,
   }
   for (int r = 0; r < nrhs; ++r)
     for (int i = n - 1; i >= 0; --i) {
-      double s = B[i * nrhs + r];
+      real s = B[i * nrhs + r];
       for (int k = i + 1; k < n; ++k) s -= A[i * n + k] * x[k * nrhs + r];
       x[i * nrhs + r] = s / A[i * n + i];
     }
@@ -238,13 +306,13 @@ namespace {
 
 // Per-node macroscopic state of the streamed populations (Sec. 2.1, 3.1).
 struct Macro {
-  double phi;
-  double rho_a[MMAX], j_a[MMAX][3];     // eq:density1, eq:momentum1
-  double rho_f, j_f[3], u[3];           // eqn:fdensity, eqn:f1momMomentum
-  double Pt[3][3];                      // P = sum f c c
-  double sum_g, q[3];                   // eqn:g0momTotalEnergy, q = sum g c
-  double rho_s, Y[MMAX], X[MMAX], m_mix, R, T, P;
-  double Pi[3];                         // rho u (1 - 3RT) - rho u^3/phi^2 (eqn:Pex)
+  real phi;
+  real rho_a[MMAX], j_a[MMAX][3];     // eq:density1, eq:momentum1
+  real rho_f, j_f[3], u[3];           // eqn:fdensity, eqn:f1momMomentum
+  real Pt[3][3];                      // P = sum f c c
+  real sum_g, q[3];                   // eqn:g0momTotalEnergy, q = sum g c
+  real rho_s, Y[MMAX], X[MMAX], m_mix, R, T, P;
+  real Pi[3];                         // rho u (1 - 3RT) - rho u^3/phi^2 (eqn:Pex)
 };
 
 struct Oracle {
@@ -253,21 +321,23 @@ struct Oracle {
   int N, M, Q, D, nl;                   // nl = number of lattices
   int energy, knudsen;
   // lattice units
-  double dt, cvel;                      // physical time step [s], dx/dt [m/s]
-  double RU;                            // R_U in lattice units per kelvin (kg/mol/K)
-  double m[MMAX], Dref[MMAX][MMAX], muref[MMAX], cvf[MMAX], U0[MMAX];
-  double Pref, d0;
-  double rho_in[2][MMAX], T_in[2];
+  real dt, cvel;                      // physical time step [s], dx/dt [m/s]
+  real RU;                            // R_U in lattice units per kelvin (kg/mol/K)
+  real m[MMAX], Dref[MMAX][MMAX], muref[MMAX], cvf[MMAX], U0[MMAX];
+  real Pref, d0, tort;                  // d0 = 2 r_p / dx; tortuosity
+  real rho_in[2][MMAX], T_in[2];
   // mechanism
   int S, Rn;
   double nu_g[RMAX][MMAX], nu_s[RMAX][SMAX], Apre[RMAX], Ea[RMAX];
-  double gamma, a_s, ms[SMAX], cvs[SMAX], Us0[SMAX], Ug0[MMAX];
+  real gamma, a_s, ms[SMAX], cvs[SMAX], Us0[SMAX], Ug0[MMAX];
   // state
-  std::vector<double> pops, pulled, phi, Tfix, Xs, Xs_new;
+  std::vector<real> pops, pulled, phi, Tfix, Xs, Xs_new;
   std::vector<Macro> mac;
   // diagnostics of the last collision
-  std::vector<double> dg_V, dg_Fk, dg_omega, dg_omega1, dg_T, dg_P, dg_rhodot, dg_kappa;
+  std::vector<real> dg_V, dg_Fk, dg_omega, dg_omega1, dg_T, dg_P, dg_rhodot, dg_kappa;
   long steps_done;
+  // initial fields (kept to rebuild the initial populations)
+  std::vector<double> X0, T0, P0, U0i, Xs_init0;
 };
 
 inline size_t PIDX(const Oracle& o, int l, int i, int n) { return ((size_t)l * o.Q + i) * o.N + n; }
@@ -285,30 +355,30 @@ int wrap(int v, int n) { return ((v % n) + n) % n; }
 // ---------------------------------------------------------------------------
 // Thermodynamics (Sec. 2.1 nomenclature, Sec. 3.1 eq:specUa..eq:H).
 // ---------------------------------------------------------------------------
-double R_species(const Oracle& o, int a) { return o.RU / o.m[a]; }            // R_a = R_U / m_a
-double U_species(const Oracle& o, int a, double T) {                          // eq:specUa
+real R_species(const Oracle& o, int a) { return o.RU / o.m[a]; }            // R_a = R_U / m_a
+real U_species(const Oracle& o, int a, real T) {                          // eq:specUa
   return o.U0[a] + o.cvf[a] * R_species(o, a) * (T - o.cfg.T_thermo);
 }
 
 // Species equilibrium (eq:27eq), quasi-equilibrium (eq:27qeq with the
 // parameterisation eq:xiPstar2) and Knudsen quasi-equilibrium (eq:fKnudsen):
 // phi rho_a Prod Psi(xi, P) with the per-axis parameters given.
-void species_form(const Oracle& o, double phi, double rho_a, const double* xi, double RaT, double* out) {
-  double P[3];
+void species_form(const Oracle& o, real phi, real rho_a, const real* xi, real RaT, real* out) {
+  real P[3];
   for (int al = 0; al < o.D; ++al) P[al] = xi[al] * xi[al] + RaT;
-  double pf[QMAX];
+  real pf[QMAX];
   product_form(o.L, xi, P, pf);
   for (int i = 0; i < o.Q; ++i) out[i] = phi * rho_a * pf[i];
 }
 
 // Macroscopic state from populations at one node (a2 + a3).
-void compute_macro(const Oracle& o, const double* fpop /* [nl][Q] */, double phi, double Tfixed, Macro& m) {
+void compute_macro(const Oracle& o, const real* fpop /* [nl][Q] */, real phi, real Tfixed, Macro& m) {
   const Lattice& L = o.L;
   m.phi = phi;
   for (int a = 0; a < o.M; ++a) {
-    double s = 0.0, j[3] = {0, 0, 0};
+    real s = 0.0, j[3] = {0, 0, 0};
     for (int i = 0; i < o.Q; ++i) {
-      double f = fpop[a * o.Q + i];
+      real f = fpop[a * o.Q + i];
       s += f;
       for (int al = 0; al < 3; ++al) j[al] += f * L.c[i][al];
     }
@@ -316,8 +386,8 @@ void compute_macro(const Oracle& o, const double* fpop /* [nl][Q] */, double phi
     for (int al = 0; al < 3; ++al) m.j_a[a][al] = j[al]; // eq:momentum1
   }
   {
-    const double* f = fpop + o.M * o.Q;
-    double s = 0.0, j[3] = {0, 0, 0}, P[3][3] = {{0}};
+    const real* f = fpop + o.M * o.Q;
+    real s = 0.0, j[3] = {0, 0, 0}, P[3][3] = {{0}};
     for (int i = 0; i < o.Q; ++i) {
       s += f[i];
       for (int al = 0; al < 3; ++al) {
@@ -332,7 +402,7 @@ void compute_macro(const Oracle& o, const double* fpop /* [nl][Q] */, double phi
   m.sum_g = 0.0;
   m.q[0] = m.q[1] = m.q[2] = 0.0;
   if (o.energy) {
-    const double* g = fpop + (o.M + 1) * o.Q;
+    const real* g = fpop + (o.M + 1) * o.Q;
     for (int i = 0; i < o.Q; ++i) {
       m.sum_g += g[i];
       for (int al = 0; al < 3; ++al) m.q[al] += g[i] * L.c[i][al];
@@ -341,17 +411,17 @@ void compute_macro(const Oracle& o, const double* fpop /* [nl][Q] */, double phi
   // composition (Sec. 2.1): rho = sum rho_a, Y_a, 1/m = sum Y_a/m_a, X_a
   m.rho_s = 0.0;
   for (int a = 0; a < o.M; ++a) m.rho_s += m.rho_a[a];
-  double inv_m = 0.0;
+  real inv_m = 0.0;
   for (int a = 0; a < o.M; ++a) { m.Y[a] = m.rho_a[a] / m.rho_s; inv_m += m.Y[a] / o.m[a]; }
   m.m_mix = 1.0 / inv_m;
   for (int a = 0; a < o.M; ++a) m.X[a] = m.m_mix * m.Y[a] / o.m[a];
   m.R = o.RU / m.m_mix;                                 // R = R_U / m
   // temperature (eq:temperature with u^2/(2 phi^2), reading R5; constant C_v)
   if (o.energy) {
-    double E = m.sum_g / (phi * m.rho_f);               // eq:totalE with the momentum lattice's rho (reading R7)
-    double w2 = 0.0;
+    real E = m.sum_g / (phi * m.rho_f);               // eq:totalE with the momentum lattice's rho (reading R7)
+    real w2 = 0.0;
     for (int al = 0; al < o.D; ++al) w2 += (m.u[al] / phi) * (m.u[al] / phi);
-    double cv = 0.0, U0m = 0.0;
+    real cv = 0.0, U0m = 0.0;
     for (int a = 0; a < o.M; ++a) {
       cv += m.Y[a] * o.cvf[a] * R_species(o, a);
       U0m += m.Y[a] * o.U0[a];
@@ -363,7 +433,7 @@ void compute_macro(const Oracle& o, const double* fpop /* [nl][Q] */, double phi
   }
   m.P = m.rho_f * m.R * m.T;                            // eqn:eosIdealGas with rho of eqn:fdensity (reading R7)
   for (int al = 0; al < 3; ++al) {
-    double w = m.u[al] / phi;
+    real w = m.u[al] / phi;
     m.Pi[al] = m.rho_f * m.u[al] * (1.0 - 3.0 * m.R * m.T) - m.rho_f * m.u[al] * w * w;
   }
 }
@@ -374,38 +444,38 @@ void compute_macro(const Oracle& o, const double* fpop /* [nl][Q] */, double phi
 // Returns gas mass production rates rhodot_f[a] (kg/m^3 per lattice time,
 // eq:totalFluidReactionRate / eq:molarToMassRates) and the new coverages.
 // ---------------------------------------------------------------------------
-void surface_source(const Oracle& o, const Macro& m, const double* Xs0, double* rhodot_f,
-                    double* Xs1, double& dU_fluid_volumetric);
+void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhodot_f,
+                    real* Xs1, real& dU_fluid_volumetric);
 
 // ---------------------------------------------------------------------------
 // One node's collision (a4 .. a9).  fin: streamed populations [nl][Q];
 // fout: post-collision populations.  Gradient inputs come from neighbours.
 // ---------------------------------------------------------------------------
 struct Grad {
-  double divu;              // d_beta u_beta
-  double dPi[3];            // d_alpha Pi_alpha (no sum)
-  double dY[MMAX][3];       // d_alpha Y_a
+  real divu;              // d_beta u_beta
+  real dPi[3];            // d_alpha Pi_alpha (no sum)
+  real dY[MMAX][3];       // d_alpha Y_a
 };
 
-void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const double* fin,
-                  double* fout, const double* Xs0, double* Xs1) {
+void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const real* fin,
+                  real* fout, const real* Xs0, real* Xs1) {
   const Lattice& L = o.L;
   const int M = o.M, Q = o.Q, D = o.D;
-  const double phi = m.phi, T = m.T, P = m.P;
+  const real phi = m.phi, T = m.T, P = m.P;
 
   // --- transport coefficients (a4) ----------------------------------------
   // synthetic binary diffusivities (reading R13): D_ab(T,P) = Dref (T/Tref)^1.5 (Pref/P)
-  double tau_ab[MMAX][MMAX];
+  real tau_ab[MMAX][MMAX];
   for (int a = 0; a < M; ++a)
     for (int b = 0; b < M; ++b) {
       if (a == b) { tau_ab[a][b] = 0.0; continue; }
-      double Dab = o.Dref[a][b] * std::pow(T / o.cfg.T_ref, 1.5) * (o.Pref / P);
+      real Dab = o.Dref[a][b] * r_pow(T / o.cfg.T_ref, 1.5) * (o.Pref / P);
       // eqn:tauab read dimensionally (reading R1): tau_ab = D_ab m_a m_b / (m R_U T)
       tau_ab[a][b] = Dab * o.m[a] * o.m[b] / (m.m_mix * o.RU * T);
     }
-  double inv_tau[MMAX], inv_tauk[MMAX], beta[MMAX];
+  real inv_tau[MMAX], inv_tauk[MMAX], beta[MMAX];
   for (int a = 0; a < M; ++a) {
-    double s = 0.0;                                      // eqn:taua
+    real s = 0.0;                                      // eqn:taua
     for (int b = 0; b < M; ++b) if (b != a) s += m.Y[b] / tau_ab[a][b];
     inv_tau[a] = s;
     // eqn:betaa: beta = dt/(2 tau + dt), written as (1/tau)/(2 + 1/tau) so that
@@ -413,9 +483,9 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
     beta[a] = inv_tau[a] / (2.0 + inv_tau[a]);
     if (o.knudsen) {
       // Knudsen diffusivity (Sec. 5.1): D^k = (phi/tortuosity)(d0/3) sqrt(8 R_U T/(pi m_a))
-      double Dk = (phi / o.cfg.tortuosity) * (o.d0 / 3.0) * std::sqrt(8.0 * o.RU * T / (PI_D * o.m[a]));
+      real Dk = (phi / o.tort) * (o.d0 / 3.0) * r_sqrt(8.0 * o.RU * T / (PI_D * o.m[a]));
       // eqn:tauak read dimensionally (reading R1): tau^k = D^k m_a / (R_U T)
-      double tk = Dk * o.m[a] / (o.RU * T);
+      real tk = Dk * o.m[a] / (o.RU * T);
       inv_tauk[a] = 1.0 / tk;
     } else {
       inv_tauk[a] = 0.0;
@@ -423,11 +493,11 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   }
 
   // --- component velocities and the diffusion-velocity solve (a6) ---------
-  double ua[MMAX][3];
+  real ua[MMAX][3];
   for (int a = 0; a < M; ++a)
     for (int al = 0; al < 3; ++al)
       ua[a][al] = (m.rho_a[a] < 1e-14 * m.rho_s) ? m.u[al] : m.j_a[a][al] / m.rho_a[a];   // R11
-  double A[MMAX * MMAX], rhs[MMAX * 3], V[MMAX * 3];
+  real A[MMAX * MMAX], rhs[MMAX * 3], V[MMAX * 3];
   for (int a = 0; a < M; ++a) {
     for (int b = 0; b < M; ++b) {
       if (a == b) A[a * M + b] = 1.0 + 0.5 * inv_tau[a] + 0.5 * inv_tauk[a];   // eqn:transform1
@@ -438,12 +508,12 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   householder_qr_solve(M, A, 3, rhs, V);
   // condition bound (reading R12): ||A||_inf * ||A^-1||_inf <= max row sum / min(1 + dt/2tau^k)
   {
-    double amax = 0.0, dmin = 1e300;
+    real amax = 0.0, dmin = 1e300;
     for (int a = 0; a < M; ++a) {
-      double rs = 0.0;
-      for (int b = 0; b < M; ++b) rs += std::fabs(A[a * M + b]);
+      real rs = 0.0;
+      for (int b = 0; b < M; ++b) rs += r_fabs(A[a * M + b]);
       if (rs > amax) amax = rs;
-      double d = 1.0 + 0.5 * inv_tauk[a];
+      real d = 1.0 + 0.5 * inv_tauk[a];
       if (d < dmin) dmin = d;
     }
     const_cast<Oracle&>(o).dg_kappa[n] = amax / dmin;
@@ -452,17 +522,17 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
     for (int al = 0; al < 3; ++al) const_cast<Oracle&>(o).dg_V[((size_t)a * 3 + al) * o.N + n] = V[a * 3 + al];
 
   // --- surface source (a10), zero without a mechanism ----------------------
-  double rhodot[MMAX];
+  real rhodot[MMAX];
   for (int a = 0; a < M; ++a) rhodot[a] = 0.0;
-  double dU_src = 0.0;
+  real dU_src = 0.0;
   if (o.S > 0) surface_source(o, m, Xs0, rhodot, Xs1, dU_src);
   for (int a = 0; a < M; ++a) const_cast<Oracle&>(o).dg_rhodot[(size_t)a * o.N + n] = rhodot[a];
 
   // --- species collision (a7): eqn:finalNumericalEquationsReactive ----------
-  double feq[MMAX][QMAX], fst[MMAX][QMAX], fk[MMAX][QMAX], fr[MMAX][QMAX];
+  real feq[MMAX][QMAX], fst[MMAX][QMAX], fk[MMAX][QMAX], fr[MMAX][QMAX];
   for (int a = 0; a < M; ++a) {
-    double RaT = R_species(o, a) * T;
-    double xi_eq[3], xi_st[3], xi_k[3] = {0, 0, 0};
+    real RaT = R_species(o, a) * T;
+    real xi_eq[3], xi_st[3], xi_k[3] = {0, 0, 0};
     for (int al = 0; al < 3; ++al) {
       xi_eq[al] = m.u[al] / phi;                         // eq:27eq
       xi_st[al] = (m.u[al] + V[a * 3 + al]) / phi;       // eq:xiPstar2 with phi (reading R2)
@@ -471,18 +541,18 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
     species_form(o, phi, m.rho_a[a], xi_st, RaT, fst[a]);
     species_form(o, phi, m.rho_a[a], xi_k, RaT, fk[a]);  // eq:fKnudsen
     // reaction source populations (eq:fsourceHetero): rhodot Prod Psi(u/phi, ...)
-    double pf[QMAX], Pp[3];
+    real pf[QMAX], Pp[3];
     for (int al = 0; al < D; ++al) Pp[al] = xi_eq[al] * xi_eq[al] + RaT;
     product_form(L, xi_eq, Pp, pf);
     for (int i = 0; i < Q; ++i) fr[a][i] = rhodot[a] * pf[i];
   }
   for (int a = 0; a < M; ++a) {
     for (int i = 0; i < Q; ++i) {
-      double F = 0.0;                                    // eqn:fStar
+      real F = 0.0;                                    // eqn:fStar
       for (int b = 0; b < M; ++b) if (b != a) F += (1.0 / tau_ab[a][b]) * (feq[b][i] - fst[b][i]);
       F *= m.Y[a];
       F += inv_tauk[a] * (fst[a][i] - fk[a][i]);
-      double f = fin[a * Q + i];
+      real f = fin[a * Q + i];
       // R^r ~ fdot^r dt (eq:R2), dt = 1
       fout[a * Q + i] = f + 2.0 * beta[a] * (feq[a][i] - f) + (beta[a] - 1.0) * F + fr[a][i];
     }
@@ -491,96 +561,96 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   // --- momentum lattice (a8): eqn:f / eqn:f_source ---------------------------
   // net Knudsen force eqn:netKnudsenForce with P X_b / D^k_b = rho_b / tau^k_b and
   // the component velocity u_b = u + V_b of the discrete system (reading R8).
-  double Fk[3] = {0, 0, 0};
+  real Fk[3] = {0, 0, 0};
   for (int b = 0; b < M; ++b)
     for (int al = 0; al < D; ++al) Fk[al] -= m.rho_a[b] * (m.u[al] + V[b * 3 + al]) * inv_tauk[b];
   for (int al = 0; al < 3; ++al) const_cast<Oracle&>(o).dg_Fk[(size_t)al * o.N + n] = Fk[al];
   // viscosity (reading R13): mu = sum_a X_a mu_a(T), mu_a = mu_ref,a (T/Tref)^mu_exp
-  double mu = 0.0;
-  for (int a = 0; a < M; ++a) mu += m.X[a] * o.muref[a] * std::pow(T / o.cfg.T_ref, o.cfg.mu_exp);
-  double omega = 1.0 / (0.5 + mu / P);                   // eq:mu with dt = 1
-  double omega1 = 1.0 / (0.5 + mu / (o.cfg.Pr * P));     // eq:lambda with lambda = mu C_p / Pr
-  double vs = o.cfg.bulk_ratio * mu;                      // bulk viscosity
+  real mu = 0.0;
+  for (int a = 0; a < M; ++a) mu += m.X[a] * o.muref[a] * r_pow(T / o.cfg.T_ref, o.cfg.mu_exp);
+  real omega = 1.0 / (0.5 + mu / P);                   // eq:mu with dt = 1
+  real omega1 = 1.0 / (0.5 + mu / (o.cfg.Pr * P));     // eq:lambda with lambda = mu C_p / Pr
+  real vs = o.cfg.bulk_ratio * mu;                      // bulk viscosity
   const_cast<Oracle&>(o).dg_omega[n] = omega;
   const_cast<Oracle&>(o).dg_omega1[n] = omega1;
-  double cv_mix = 0.0;
+  real cv_mix = 0.0;
   for (int a = 0; a < M; ++a) cv_mix += m.Y[a] * o.cvf[a] * R_species(o, a);
   // bulk-viscosity bracket of eqn:Pex; isothermal lattices have no energy
   // equation, so the R/C_v part (from dT/dt) is absent there.
-  double bulk = -vs + mu * (2.0 / D - (o.energy ? m.R / cv_mix : 0.0));
-  double uex[3], xi_ex[3], Pex[3];
+  real bulk = -vs + mu * (2.0 / D - (o.energy ? m.R / cv_mix : 0.0));
+  real uex[3], xi_ex[3], Pex[3];
   for (int al = 0; al < 3; ++al) uex[al] = m.u[al] + Fk[al] / (omega * m.rho_f);   // reading R3
   for (int al = 0; al < D; ++al) {
-    double Peq = m.R * T + (m.u[al] / phi) * (m.u[al] / phi);                      // eqn:Peq
+    real Peq = m.R * T + (m.u[al] / phi) * (m.u[al] / phi);                      // eqn:Peq
     Pex[al] = Peq + bulk * gr.divu / (phi * m.rho_f)
               + ((2.0 - omega) / (2.0 * phi * m.rho_f * omega)) * gr.dPi[al];      // eqn:Pex
     xi_ex[al] = uex[al] / phi;
   }
-  double pfx[QMAX];
+  real pfx[QMAX];
   product_form(L, xi_ex, Pex, pfx);
   // post-collision mixture density (eq:rho_pc): phi rho_pc = phi rho + sum rhodot dt
-  double sum_rd = 0.0;
+  real sum_rd = 0.0;
   for (int a = 0; a < M; ++a) sum_rd += rhodot[a];
-  double rho_pc = m.rho_f + sum_rd / phi;
+  real rho_pc = m.rho_f + sum_rd / phi;
   for (int i = 0; i < Q; ++i) {
-    double fex = phi * m.rho_f * pfx[i];                                          // eq:feqmix
-    double f = fin[M * Q + i];
+    real fex = phi * m.rho_f * pfx[i];                                          // eq:feqmix
+    real f = fin[M * Q + i];
     fout[M * Q + i] = f + omega * (fex - f) + (rho_pc / m.rho_f * fex - fex);     // eqn:f_source
   }
 
   // --- energy lattice (a9): eqn:g / eqn:g_source -----------------------------
   if (o.energy) {
-    double U = 0.0, H = 0.0, Ha[MMAX];
+    real U = 0.0, H = 0.0, Ha[MMAX];
     for (int a = 0; a < M; ++a) {
-      double Ua = U_species(o, a, T);
+      real Ua = U_species(o, a, T);
       Ha[a] = Ua + R_species(o, a) * T;                  // H_a = U_a + R_a T (Mayer)
       U += m.Y[a] * Ua;                                  // eq:U
       H += m.Y[a] * Ha[a];                               // eq:H
     }
-    double geq[QMAX];
+    real geq[QMAX];
     energy_equilibrium(L, phi, m.rho_f, m.u, m.R * T, U, geq);
-    double w2 = 0.0;
+    real w2 = 0.0;
     for (int al = 0; al < D; ++al) w2 += (m.u[al] / phi) * (m.u[al] / phi);
-    double qeq[3] = {0, 0, 0};
+    real qeq[3] = {0, 0, 0};
     for (int al = 0; al < D; ++al) qeq[al] = (H + 0.5 * w2) * m.rho_f * m.u[al];   // eqn:geq1mom
     // equilibrium pressure tensor of the momentum lattice (eq:Peq, reading R6)
-    double Peq[3][3];
+    real Peq[3][3];
     for (int al = 0; al < 3; ++al)
       for (int be = 0; be < 3; ++be)
         Peq[al][be] = phi * m.rho_f * (m.u[al] / phi) * (m.u[be] / phi) + (al == be ? phi * m.rho_f * m.R * T : 0.0);
-    double qdiff[3] = {0, 0, 0}, qcorr[3] = {0, 0, 0}, qex[3] = {0, 0, 0}, qst[3] = {0, 0, 0};
+    real qdiff[3] = {0, 0, 0}, qcorr[3] = {0, 0, 0}, qex[3] = {0, 0, 0}, qst[3] = {0, 0, 0};
     for (int al = 0; al < D; ++al) {
       // diffusion velocities relative to the mass average: eq:totmomSpec with
       // u_a = u + V_a implies sum_a rho_a V_a = 0, which the discrete system
       // eqn:transform1 satisfies only up to the weak-coupling drift (reading R22)
-      double Vbar = 0.0;
+      real Vbar = 0.0;
       for (int a = 0; a < M; ++a) Vbar += m.Y[a] * V[a * 3 + al];
-      double sV = 0.0, sdY = 0.0;
+      real sV = 0.0, sdY = 0.0;
       for (int a = 0; a < M; ++a) { sV += Ha[a] * m.Y[a] * (V[a * 3 + al] - Vbar); sdY += Ha[a] * gr.dY[a][al]; }
       qdiff[al] = (omega1 / (omega - omega1)) * m.rho_f * sV;                      // eq:interdiffusion
       qcorr[al] = 0.5 * ((omega1 - 2.0) / (omega1 - omega)) * P * phi * sdY;        // eq:corrFourier
       qex[al] = m.u[al] * (omega / (omega - omega1)) * bulk * gr.divu / phi
                 - 0.5 * (m.u[al] / phi) * gr.dPi[al];                                // eqn:qex
-      double uP = 0.0;
+      real uP = 0.0;
       for (int be = 0; be < D; ++be) uP += (m.u[be] / phi) * (m.Pt[al][be] - Peq[al][be]);
       qst[al] = m.q[al] - uP + qdiff[al] + qcorr[al] + qex[al];                     // eq:gstareq1mom
     }
     // source distribution (eqn:g0mom_source): same equilibrium with the
     // post-reaction density and internal energy (zero change without reactions)
-    double gsrc[QMAX];
+    real gsrc[QMAX];
     bool have_src = (o.S > 0);
     if (have_src) {
-      double U_pc = (phi * m.rho_f * U + dU_src) / (phi * rho_pc);
+      real U_pc = (phi * m.rho_f * U + dU_src) / (phi * rho_pc);
       energy_equilibrium(L, phi, rho_pc, m.u, m.R * T, U_pc, gsrc);
     }
-    const double* g = fin + (M + 1) * Q;
+    const real* g = fin + (M + 1) * Q;
     for (int i = 0; i < Q; ++i) {
       int c2 = 0;
       for (int al = 0; al < D; ++al) c2 += L.c[i][al] * L.c[i][al];
-      double gst = geq[i];                                                           // eq:gstar
+      real gst = geq[i];                                                           // eq:gstar
       if (c2 == 1)
         for (int al = 0; al < D; ++al) gst += 0.5 * L.c[i][al] * (qst[al] - qeq[al]);
-      double src = have_src ? (gsrc[i] - geq[i]) : 0.0;
+      real src = have_src ? (gsrc[i] - geq[i]) : 0.0;
       fout[(M + 1) * Q + i] = g[i] + omega1 * (geq[i] - g[i]) + (omega - omega1) * (gst - g[i]) + src;
     }
   }
@@ -591,20 +661,20 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
 // prescribed composition, pressure and temperature, moving with the velocity
 // of the adjacent interior node of the same step.
 // ---------------------------------------------------------------------------
-void inlet_ghost(const Oracle& o, int side, double phi, const double* u, double* ghost /* [nl][Q] */) {
+void inlet_ghost(const Oracle& o, int side, real phi, const real* u, real* ghost /* [nl][Q] */) {
   const int M = o.M, Q = o.Q;
-  double T = o.T_in[side];
-  double rho = 0.0;
+  real T = o.T_in[side];
+  real rho = 0.0;
   for (int a = 0; a < M; ++a) rho += o.rho_in[side][a];
-  double inv_m = 0.0;
+  real inv_m = 0.0;
   for (int a = 0; a < M; ++a) inv_m += (o.rho_in[side][a] / rho) / o.m[a];
-  double R = o.RU * inv_m;
-  double xi[3];
+  real R = o.RU * inv_m;
+  real xi[3];
   for (int al = 0; al < 3; ++al) xi[al] = u[al] / phi;
   for (int a = 0; a < M; ++a) species_form(o, phi, o.rho_in[side][a], xi, R_species(o, a) * T, ghost + a * Q);
   species_form(o, phi, rho, xi, R * T, ghost + M * Q);
   if (o.energy) {
-    double U = 0.0;
+    real U = 0.0;
     for (int a = 0; a < M; ++a) U += (o.rho_in[side][a] / rho) * U_species(o, a, T);
     energy_equilibrium(o.L, phi, rho, u, R * T, U, ghost + (M + 1) * Q);
   }
@@ -646,15 +716,15 @@ void stream(Oracle& o) {
     for (int z = 0; z < nz; ++z)
       for (int y = 0; y < ny; ++y) {
         int nb = node_index(o, xb, y, z), na = node_index(o, xa, y, z);
-        double js = 0.0, jf[3] = {0, 0, 0};
+        real js = 0.0, jf[3] = {0, 0, 0};
         for (int i = 0; i < Q; ++i) {
-          double f = o.pulled[PIDX(o, o.M, i, na)];
+          real f = o.pulled[PIDX(o, o.M, i, na)];
           js += f;
           for (int al = 0; al < 3; ++al) jf[al] += f * L.c[i][al];
         }
-        double rho_f = js / o.phi[na];
-        double u[3] = {jf[0] / rho_f, jf[1] / rho_f, jf[2] / rho_f};
-        double ghost[(MMAX + 2) * QMAX];
+        real rho_f = js / o.phi[na];
+        real u[3] = {jf[0] / rho_f, jf[1] / rho_f, jf[2] / rho_f};
+        real ghost[(MMAX + 2) * QMAX];
         inlet_ghost(o, side, o.phi[nb], u, ghost);
         for (int i = 0; i < Q; ++i)
           if (missing[(size_t)i * o.N + nb])
@@ -666,7 +736,7 @@ void stream(Oracle& o) {
 void compute_all_macro(Oracle& o) {
 #pragma omp parallel for schedule(static)
   for (int n = 0; n < o.N; ++n) {
-    double f[(MMAX + 2) * QMAX];
+    real f[(MMAX + 2) * QMAX];
     for (int l = 0; l < o.nl; ++l)
       for (int i = 0; i < o.Q; ++i) f[l * o.Q + i] = o.pulled[PIDX(o, l, i, n)];
     compute_macro(o, f, o.phi[n], o.Tfix[n], o.mac[n]);
@@ -690,7 +760,7 @@ void gradients(const Oracle& o, int n, Grad& gr) {
     if (sx >= o.cfg.nx) sx = (o.cfg.bc_hi == 0) ? wrap(sx, o.cfg.nx) : o.cfg.nx - 1;
     int sy = wrap(y + L.c[i][1], o.cfg.ny), sz = wrap(z + L.c[i][2], o.cfg.nz);
     const Macro& mn = o.mac[node_index(o, sx, sy, sz)];
-    double w = 3.0 * lattice_weight(L, i);
+    real w = 3.0 * lattice_weight(L, i);
     for (int al = 0; al < L.D; ++al) {
       if (L.c[i][al] == 0) continue;
       gr.divu += w * L.c[i][al] * mn.u[al];
@@ -706,14 +776,14 @@ void gradients(const Oracle& o, int n, Grad& gr) {
 // Rates of progress r_k [mol m^-2 s^-1] by mass action with Arrhenius
 // constants k = A exp(-Ea/(R_U T)) (reading R15).  c_gas in mol/m^3 (fluid),
 // theta = surface concentration Gamma X^(s) in mol/m^2.
-void mass_action_rates(const Oracle& o, double T, const double* cg, const double* cs, double* r) {
+void mass_action_rates(const Oracle& o, real T, const real* cg, const real* cs, real* r) {
   for (int k = 0; k < o.Rn; ++k) {
-    double kr = o.Apre[k] * std::exp(-o.Ea[k] / (R_UNIV * T));
-    double v = kr;
+    real kr = o.Apre[k] * r_exp(-o.Ea[k] / (R_UNIV * T));
+    real v = kr;
     for (int a = 0; a < o.M; ++a)
-      if (o.nu_g[k][a] < 0) v *= std::pow(std::max(cg[a], 0.0), -o.nu_g[k][a]);
+      if (o.nu_g[k][a] < 0) v *= r_pow(rmax(cg[a], 0.0), -o.nu_g[k][a]);
     for (int s = 0; s < o.S; ++s)
-      if (o.nu_s[k][s] < 0) v *= std::pow(std::max(cs[s], 0.0), -o.nu_s[k][s]);
+      if (o.nu_s[k][s] < 0) v *= r_pow(rmax(cs[s], 0.0), -o.nu_s[k][s]);
     r[k] = v;
   }
 }
@@ -721,29 +791,29 @@ void mass_action_rates(const Oracle& o, double T, const double* cg, const double
 // Backward Euler in the extents xi_k [mol/m^2] over the physical step dt:
 // xi = dt * r(c_gas0 + (a_s/phi) nu_g^T xi, theta0 + nu_s^T xi), solved by
 // Newton with a finite-difference-free analytic Jacobian of mass action.
-void surface_source(const Oracle& o, const Macro& m, const double* Xs0, double* rhodot_f,
-                    double* Xs1, double& dU_fluid_volumetric) {
+void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhodot_f,
+                    real* Xs1, real& dU_fluid_volumetric) {
   const int M = o.M, S = o.S, Rn = o.Rn;
-  const double T = m.T;
-  const double dtp = o.dt;                        // physical seconds
-  double cg0[MMAX], cs0[SMAX];
+  const real T = m.T;
+  const real dtp = o.dt;                        // physical seconds
+  real cg0[MMAX], cs0[SMAX];
   for (int a = 0; a < M; ++a) cg0[a] = m.rho_a[a] / o.m[a];                 // mol/m^3 of fluid
   for (int s = 0; s < S; ++s) cs0[s] = o.gamma * Xs0[s];                    // eq:surfaceMoleFractions
-  double xi[RMAX];
+  real xi[RMAX];
   for (int k = 0; k < Rn; ++k) xi[k] = 0.0;
-  double scale = o.a_s / m.phi;                   // surface area per fluid volume
+  real scale = o.a_s / m.phi;                   // surface area per fluid volume
   for (int it = 0; it < 30; ++it) {
-    double cg[MMAX], cs[SMAX];
+    real cg[MMAX], cs[SMAX];
     for (int a = 0; a < M; ++a) { cg[a] = cg0[a]; for (int k = 0; k < Rn; ++k) cg[a] += scale * o.nu_g[k][a] * xi[k]; }
     for (int s = 0; s < S; ++s) { cs[s] = cs0[s]; for (int k = 0; k < Rn; ++k) cs[s] += o.nu_s[k][s] * xi[k]; }
-    double r[RMAX];
+    real r[RMAX];
     mass_action_rates(o, T, cg, cs, r);
-    double Fv[RMAX], J[RMAX * RMAX];
+    real Fv[RMAX], J[RMAX * RMAX];
     for (int k = 0; k < Rn; ++k) Fv[k] = xi[k] - dtp * r[k];
     // Jacobian: dF_k/dxi_l = delta_kl - dt * dr_k/dxi_l
     for (int k = 0; k < Rn; ++k)
       for (int l = 0; l < Rn; ++l) {
-        double d = 0.0;
+        real d = 0.0;
         for (int a = 0; a < M; ++a)
           if (o.nu_g[k][a] < 0 && cg[a] > 0) d += r[k] * (-o.nu_g[k][a]) / cg[a] * scale * o.nu_g[l][a];
         for (int s = 0; s < S; ++s)
@@ -751,23 +821,23 @@ void surface_source(const Oracle& o, const Macro& m, const double* Xs0, double* 
         J[k * Rn + l] = (k == l ? 1.0 : 0.0) - dtp * d;
       }
     // Gaussian elimination with partial pivoting on J dxi = -F
-    double Ab[RMAX * (RMAX + 1)];
+    real Ab[RMAX * (RMAX + 1)];
     for (int k = 0; k < Rn; ++k) {
       for (int l = 0; l < Rn; ++l) Ab[k * (Rn + 1) + l] = J[k * Rn + l];
       Ab[k * (Rn + 1) + Rn] = -Fv[k];
     }
     for (int c = 0; c < Rn; ++c) {
       int p = c;
-      for (int k = c + 1; k < Rn; ++k) if (std::fabs(Ab[k * (Rn + 1) + c]) > std::fabs(Ab[p * (Rn + 1) + c])) p = k;
+      for (int k = c + 1; k < Rn; ++k) if (r_fabs(Ab[k * (Rn + 1) + c]) > r_fabs(Ab[p * (Rn + 1) + c])) p = k;
       if (p != c) for (int l = 0; l <= Rn; ++l) std::swap(Ab[c * (Rn + 1) + l], Ab[p * (Rn + 1) + l]);
       for (int k = c + 1; k < Rn; ++k) {
-        double f = Ab[k * (Rn + 1) + c] / Ab[c * (Rn + 1) + c];
+        real f = Ab[k * (Rn + 1) + c] / Ab[c * (Rn + 1) + c];
         for (int l = c; l <= Rn; ++l) Ab[k * (Rn + 1) + l] -= f * Ab[c * (Rn + 1) + l];
       }
     }
-    double dxi[RMAX];
+    real dxi[RMAX];
     for (int k = Rn - 1; k >= 0; --k) {
-      double s = Ab[k * (Rn + 1) + Rn];
+      real s = Ab[k * (Rn + 1) + Rn];
       for (int l = k + 1; l < Rn; ++l) s -= Ab[k * (Rn + 1) + l] * dxi[l];
       dxi[k] = s / Ab[k * (Rn + 1) + k];
     }
@@ -775,44 +845,44 @@ void surface_source(const Oracle& o, const Macro& m, const double* Xs0, double* 
     // action keeps every concentration >= 0, so a Newton step that would take
     // a non-negative concentration below zero is shortened (to 9/10 of the
     // distance to zero)
-    double alpha = 1.0;
+    real alpha = 1.0;
     for (int a = 0; a < M; ++a) {
-      double d = 0.0;
+      real d = 0.0;
       for (int k = 0; k < Rn; ++k) d += scale * o.nu_g[k][a] * dxi[k];
-      if (cg[a] >= 0.0 && cg[a] + d < 0.0) alpha = std::min(alpha, 0.9 * cg[a] / (-d));
+      if (cg[a] >= 0.0 && cg[a] + d < 0.0) alpha = rmin(alpha, 0.9 * cg[a] / (-d));
     }
     for (int s = 0; s < S; ++s) {
-      double d = 0.0;
+      real d = 0.0;
       for (int k = 0; k < Rn; ++k) d += o.nu_s[k][s] * dxi[k];
-      if (cs[s] >= 0.0 && cs[s] + d < 0.0) alpha = std::min(alpha, 0.9 * cs[s] / (-d));
+      if (cs[s] >= 0.0 && cs[s] + d < 0.0) alpha = rmin(alpha, 0.9 * cs[s] / (-d));
     }
-    double dmax = 0.0, xmax = 0.0;
+    real dmax = 0.0, xmax = 0.0;
     for (int k = 0; k < Rn; ++k) {
       xi[k] += alpha * dxi[k];
-      dmax = std::max(dmax, std::fabs(alpha * dxi[k]));
-      xmax = std::max(xmax, std::fabs(xi[k]));
+      dmax = rmax(dmax, r_fabs(alpha * dxi[k]));
+      xmax = rmax(xmax, r_fabs(xi[k]));
     }
     if (alpha == 1.0 && dmax <= 1e-14 * (xmax + 1e-300)) break;
   }
   // gas production per unit volume of porous medium over dt (eq:totalFluidReactionRate,
   // eq:molarToMassRates), converted to kg/m^3 per lattice time step
   for (int a = 0; a < M; ++a) {
-    double dn = 0.0;
+    real dn = 0.0;
     for (int k = 0; k < Rn; ++k) dn += o.nu_g[k][a] * xi[k];
     rhodot_f[a] = o.a_s * o.m[a] * dn;            // [kg/m^3 of REV] per step
   }
   for (int s = 0; s < S; ++s) {
-    double dn = 0.0;
+    real dn = 0.0;
     for (int k = 0; k < Rn; ++k) dn += o.nu_s[k][s] * xi[k];
     Xs1[s] = Xs0[s] + dn / o.gamma;               // eq:totalSurfaceReactionRate (no edge term)
   }
   // Unified internal energy (eq:temperatureCell, eq:InternalEnergyCell_PC): at
   // fixed temperature the fluid gains what the adsorbed phase loses; molar
   // internal energies U_s(T) = U0_s + cv_s R_U (T - T_thermo).
-  double dUs = 0.0;
+  real dUs = 0.0;
   for (int s = 0; s < S; ++s) {
-    double Us = o.Us0[s] + o.cvs[s] * R_UNIV * (T - o.cfg.T_thermo);
-    double dn = 0.0;
+    real Us = o.Us0[s] + o.cvs[s] * R_UNIV * (T - o.cfg.T_thermo);
+    real dn = 0.0;
     for (int k = 0; k < Rn; ++k) dn += o.nu_s[k][s] * xi[k];
     dUs += o.a_s * dn * Us;                       // J/m^3 of REV
   }
@@ -824,6 +894,98 @@ void surface_source(const Oracle& o, const Macro& m, const double* Xs0, double* 
 // ===========================================================================
 // C API used by oracle/__init__.py
 // ===========================================================================
+namespace {
+
+// Initial populations: equilibria of the initial macroscopic fields.
+void init_populations(Oracle* o) {
+  const int N = o->N;
+  for (int n = 0; n < N; ++n) {
+    real T = o->T0[n], P = o->P0[n], ph = o->phi[n];
+    real rho_a[MMAX], rho = 0.0;
+    for (int a = 0; a < o->M; ++a) {
+      rho_a[a] = P * o->X0[(size_t)a * N + n] * o->m[a] / (R_UNIV * T);
+      rho += rho_a[a];
+    }
+    real inv_m = 0.0;
+    for (int a = 0; a < o->M; ++a) inv_m += (rho_a[a] / rho) / o->m[a];
+    real R = o->RU * inv_m;
+    real u[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
+    if (!o->U0i.empty())
+      for (int al = 0; al < o->D; ++al) u[al] = o->U0i[(size_t)al * N + n] / o->cvel;
+    for (int al = 0; al < 3; ++al) xi[al] = u[al] / ph;
+    real f[QMAX];
+    for (int a = 0; a < o->M; ++a) {
+      species_form(*o, ph, rho_a[a], xi, R_species(*o, a) * T, f);
+      for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, a, i, n)] = f[i];
+    }
+    species_form(*o, ph, rho, xi, R * T, f);
+    for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, o->M, i, n)] = f[i];
+    if (o->energy) {
+      real U = 0.0;
+      for (int a = 0; a < o->M; ++a) U += (rho_a[a] / rho) * U_species(*o, a, T);
+      energy_equilibrium(o->L, ph, rho, u, R * T, U, f);
+      for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, o->M + 1, i, n)] = f[i];
+    }
+  }
+}
+
+// One node's collision with its gradients, from the streamed populations.
+void collide_at(Oracle* o, int n, real* fout) {
+  Grad gr;
+  gradients(*o, n, gr);
+  real fin[(MMAX + 2) * QMAX];
+  for (int l = 0; l < o->nl; ++l)
+    for (int i = 0; i < o->Q; ++i) fin[l * o->Q + i] = o->pulled[PIDX(*o, l, i, n)];
+  real xs0[SMAX], xs1[SMAX];
+  for (int s = 0; s < o->S; ++s) xs0[s] = o->Xs[(size_t)s * o->N + n];
+  collide_node(*o, n, o->mac[n], gr, fin, fout, xs0, xs1);
+  for (int s = 0; s < o->S; ++s) o->Xs_new[(size_t)s * o->N + n] = xs1[s];
+}
+
+// Macroscopic fields of the current state (value, or derivative `lane`).
+void moments_lane(Oracle* o, int which, int lane, double* out) {
+  const int N = o->N, M = o->M, D = o->D;
+  if (which == 8) {
+    for (size_t k = 0; k < (size_t)o->S * N; ++k) out[k] = comp(o->Xs[k], lane);
+    return;
+  }
+  stream(*o);
+  compute_all_macro(*o);
+  if (which == 6 || which == 7) {
+    // the diffusion velocities need the collision's transport coefficients;
+    // run the collision into a scratch buffer and read its diagnostics
+    std::vector<real> keep_xs = o->Xs_new;
+#pragma omp parallel for schedule(static)
+    for (int n = 0; n < N; ++n) {
+      real fout[(MMAX + 2) * QMAX];
+      collide_at(o, n, fout);
+    }
+    o->Xs_new = keep_xs;
+  }
+  for (int n = 0; n < N; ++n) {
+    const Macro& m = o->mac[n];
+    switch (which) {
+      case 0: for (int a = 0; a < M; ++a) out[(size_t)a * N + n] = comp(m.rho_a[a], lane); break;
+      case 1: for (int a = 0; a < M; ++a) for (int al = 0; al < D; ++al)
+                out[((size_t)a * D + al) * N + n] = comp(m.j_a[a][al], lane); break;
+      case 2: out[n] = comp(m.rho_f, lane); break;
+      case 3: for (int al = 0; al < D; ++al) out[(size_t)al * N + n] = comp(m.u[al], lane); break;
+      case 4: out[n] = comp(m.T, lane); break;
+      case 5: out[n] = comp(m.P * o->cvel * o->cvel, lane); break;
+      case 6: for (int a = 0; a < M; ++a) for (int al = 0; al < D; ++al)
+                out[((size_t)a * D + al) * N + n] = comp(o->dg_V[((size_t)a * 3 + al) * N + n], lane); break;
+      case 7: for (int a = 0; a < M; ++a) for (int al = 0; al < D; ++al)
+                out[((size_t)a * D + al) * N + n] =
+                    comp(m.rho_a[a] * (m.u[al] + o->dg_V[((size_t)a * 3 + al) * N + n]) * o->cvel / o->m[a], lane);
+              break;
+      case 9: out[n] = comp(m.rho_s, lane); break;
+      default: break;
+    }
+  }
+}
+
+}  // namespace
+
 extern "C" {
 
 void* oc_create(const oc_config* c) {
@@ -844,29 +1006,29 @@ void* oc_create(const oc_config* c) {
 #endif
   // lattice scaling (reading R14): max_a R_a T_scale dt^2/dx^2 = theta_max
   double mmin = 1e300;
-  for (int a = 0; a < o->M; ++a) mmin = std::min(mmin, c->molar_mass[a]);
-  o->dt = c->dx * std::sqrt(c->theta_max * mmin / (R_UNIV * c->T_scale));
-  o->cvel = c->dx / o->dt;
-  double c2 = o->cvel * o->cvel;
+  for (int a = 0; a < o->M; ++a) mmin = rmin(mmin, c->molar_mass[a]);
+  const double dt = c->dx * std::sqrt(c->theta_max * mmin / (R_UNIV * c->T_scale));
+  const double cvel = c->dx / dt;
+  const double c2 = cvel * cvel;
+  o->dt = dt;
+  o->cvel = cvel;
   o->RU = R_UNIV / c2;
   for (int a = 0; a < o->M; ++a) {
     o->m[a] = c->molar_mass[a];
-    o->muref[a] = c->mu_ref[a] / (o->cvel * c->dx);          // mu dt/dx^2
+    o->muref[a] = c->mu_ref[a] / (cvel * c->dx);          // mu dt/dx^2
     o->cvf[a] = c->cv_factor[a];
     o->U0[a] = c->U0[a] / c2;
-    for (int b = 0; b < o->M; ++b) o->Dref[a][b] = c->D_ref[a * o->M + b] / (o->cvel * c->dx);
+    for (int b = 0; b < o->M; ++b) o->Dref[a][b] = c->D_ref[a * o->M + b] / (cvel * c->dx);
   }
   o->Pref = c->P_ref / c2;
   o->d0 = 2.0 * c->pore_radius / c->dx;
+  o->tort = c->tortuosity;
   const double* Xin[2] = {c->X_in_lo, c->X_in_hi};
   double Tin[2] = {c->T_in_lo, c->T_in_hi}, Pin[2] = {c->P_in_lo, c->P_in_hi};
   for (int s = 0; s < 2; ++s) {
     o->T_in[s] = Tin[s];
-    double mm = 0.0;
-    for (int a = 0; a < o->M; ++a) mm += Xin[s][a] * o->m[a];
     // rho_a = P X_a m_a / (R_U T)  (Dalton + ideal gas, Sec. 2.1), kg/m^3
-    for (int a = 0; a < o->M; ++a) o->rho_in[s][a] = Pin[s] * Xin[s][a] * o->m[a] / (R_UNIV * Tin[s]);
-    (void)mm;
+    for (int a = 0; a < o->M; ++a) o->rho_in[s][a] = Pin[s] * Xin[s][a] * c->molar_mass[a] / (R_UNIV * Tin[s]);
   }
   o->S = c->S;
   o->Rn = c->R;
@@ -886,53 +1048,31 @@ void* oc_create(const oc_config* c) {
     }
     for (int a = 0; a < o->M; ++a) o->Ug0[a] = c->gas_U0_molar[a];
   }
-  size_t NP = (size_t)o->nl * o->Q * o->N;
+  const size_t N = o->N;
+  size_t NP = (size_t)o->nl * o->Q * N;
   o->pops.assign(NP, 0.0);
   o->pulled.assign(NP, 0.0);
-  o->phi.assign(c->porosity, c->porosity + o->N);
-  o->Tfix.assign(c->T_init, c->T_init + o->N);
-  o->mac.resize(o->N);
-  o->dg_V.assign((size_t)MMAX * 3 * o->N, 0.0);
-  o->dg_Fk.assign((size_t)3 * o->N, 0.0);
-  o->dg_omega.assign(o->N, 0.0);
-  o->dg_omega1.assign(o->N, 0.0);
-  o->dg_kappa.assign(o->N, 0.0);
-  o->dg_rhodot.assign((size_t)MMAX * o->N, 0.0);
+  o->phi.assign(c->porosity, c->porosity + N);
+  o->Tfix.assign(c->T_init, c->T_init + N);
+  o->mac.resize(N);
+  o->dg_V.assign((size_t)MMAX * 3 * N, 0.0);
+  o->dg_Fk.assign((size_t)3 * N, 0.0);
+  o->dg_omega.assign(N, 0.0);
+  o->dg_omega1.assign(N, 0.0);
+  o->dg_kappa.assign(N, 0.0);
+  o->dg_rhodot.assign((size_t)MMAX * N, 0.0);
   if (o->S > 0) {
-    o->Xs.assign((size_t)o->S * o->N, 0.0);
+    o->Xs.assign((size_t)o->S * N, 0.0);
     for (int s = 0; s < o->S; ++s)
-      for (int n = 0; n < o->N; ++n) o->Xs[(size_t)s * o->N + n] = c->Xs_init[s];
+      for (size_t n = 0; n < N; ++n) o->Xs[(size_t)s * N + n] = c->Xs_init[s];
     o->Xs_new = o->Xs;
   }
-  // initial populations: equilibria of the initial macroscopic fields
-  for (int n = 0; n < o->N; ++n) {
-    double T = c->T_init[n], P = c->P_init[n], ph = o->phi[n];
-    double rho_a[MMAX], rho = 0.0;
-    for (int a = 0; a < o->M; ++a) {
-      rho_a[a] = P * c->X_init[(size_t)a * o->N + n] * o->m[a] / (R_UNIV * T);
-      rho += rho_a[a];
-    }
-    double inv_m = 0.0;
-    for (int a = 0; a < o->M; ++a) inv_m += (rho_a[a] / rho) / o->m[a];
-    double R = o->RU * inv_m;
-    double u[3] = {0, 0, 0}, xi[3] = {0, 0, 0};
-    if (c->U_init)
-      for (int al = 0; al < o->D; ++al) u[al] = c->U_init[(size_t)al * o->N + n] / o->cvel;
-    for (int al = 0; al < 3; ++al) xi[al] = u[al] / ph;
-    double f[QMAX];
-    for (int a = 0; a < o->M; ++a) {
-      species_form(*o, ph, rho_a[a], xi, R_species(*o, a) * T, f);
-      for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, a, i, n)] = f[i];
-    }
-    species_form(*o, ph, rho, xi, R * T, f);
-    for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, o->M, i, n)] = f[i];
-    if (o->energy) {
-      double U = 0.0;
-      for (int a = 0; a < o->M; ++a) U += (rho_a[a] / rho) * U_species(*o, a, T);
-      energy_equilibrium(o->L, ph, rho, u, R * T, U, f);
-      for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, o->M + 1, i, n)] = f[i];
-    }
-  }
+  if (o->S > 0) o->Xs_init0.assign(c->Xs_init, c->Xs_init + o->S);
+  o->X0.assign(c->X_init, c->X_init + (size_t)o->M * N);
+  o->T0.assign(c->T_init, c->T_init + N);
+  o->P0.assign(c->P_init, c->P_init + N);
+  if (c->U_init) o->U0i.assign(c->U_init, c->U_init + (size_t)3 * N);
+  init_populations(o);
   o->steps_done = 0;
   return o;
 }
@@ -947,11 +1087,20 @@ int oc_threads(void) {
 #endif
 }
 
+// Number of derivative lanes of this build (0: the plain FP64 build).
+int oc_lanes(void) {
+#ifdef ORACLE_DUAL
+  return NT;
+#else
+  return 0;
+#endif
+}
+
 void oc_info(void* h, double* out) {
   Oracle* o = (Oracle*)h;
-  out[0] = o->dt;
-  out[1] = o->cvel;
-  out[2] = o->RU;
+  out[0] = comp(o->dt, -1);
+  out[1] = comp(o->cvel, -1);
+  out[2] = comp(o->RU, -1);
   out[3] = o->nl;
   out[4] = o->Q;
   out[5] = o->D;
@@ -966,44 +1115,41 @@ void oc_step(void* h, int nsteps) {
     compute_all_macro(*o);
 #pragma omp parallel for schedule(static)
     for (int n = 0; n < o->N; ++n) {
-      Grad gr;
-      gradients(*o, n, gr);
-      double fin[(MMAX + 2) * QMAX], fout[(MMAX + 2) * QMAX];
-      for (int l = 0; l < o->nl; ++l)
-        for (int i = 0; i < o->Q; ++i) fin[l * o->Q + i] = o->pulled[PIDX(*o, l, i, n)];
-      double xs0[SMAX], xs1[SMAX];
-      for (int s = 0; s < o->S; ++s) xs0[s] = o->Xs[(size_t)s * o->N + n];
-      collide_node(*o, n, o->mac[n], gr, fin, fout, xs0, xs1);
+      real fout[(MMAX + 2) * QMAX];
+      collide_at(o, n, fout);
       for (int l = 0; l < o->nl; ++l)
         for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, l, i, n)] = fout[l * o->Q + i];
-      for (int s = 0; s < o->S; ++s) o->Xs_new[(size_t)s * o->N + n] = xs1[s];
     }
     if (o->S > 0) o->Xs.swap(o->Xs_new);
     o->steps_done++;
   }
 }
 
-void oc_get_pops(void* h, double* out) {
+// Stored populations (lane < 0: values; lane k: derivative k).
+void oc_get_pops_lane(void* h, int lane, double* out) {
   Oracle* o = (Oracle*)h;
-  std::memcpy(out, o->pops.data(), o->pops.size() * sizeof(double));
+  for (size_t k = 0; k < o->pops.size(); ++k) out[k] = comp(o->pops[k], lane);
 }
 
+void oc_get_pops(void* h, double* out) { oc_get_pops_lane(h, -1, out); }
+
+// Replaces the populations (derivative parts set to zero).
 void oc_set_pops(void* h, const double* in) {
   Oracle* o = (Oracle*)h;
-  std::memcpy(o->pops.data(), in, o->pops.size() * sizeof(double));
+  for (size_t k = 0; k < o->pops.size(); ++k) o->pops[k] = in[k];
 }
 
 // Streamed (pre-collision) populations of the last step.
 void oc_get_pulled(void* h, double* out) {
   Oracle* o = (Oracle*)h;
-  std::memcpy(out, o->pulled.data(), o->pulled.size() * sizeof(double));
+  for (size_t k = 0; k < o->pulled.size(); ++k) out[k] = comp(o->pulled[k], -1);
 }
 
 // Diagnostics of the last collision: which = 0 V[M][3], 1 Fk[3], 2 omega,
 // 3 omega1, 4 kappa bound, 5 rhodot[M]; node-major blocks of N.
 void oc_get_diag(void* h, int which, double* out) {
   Oracle* o = (Oracle*)h;
-  const std::vector<double>* v = nullptr;
+  const std::vector<real>* v = nullptr;
   size_t cnt = 0;
   switch (which) {
     case 0: v = &o->dg_V; cnt = (size_t)o->M * 3 * o->N; break;
@@ -1014,74 +1160,65 @@ void oc_get_diag(void* h, int which, double* out) {
     case 5: v = &o->dg_rhodot; cnt = (size_t)o->M * o->N; break;
     default: return;
   }
-  std::memcpy(out, v->data(), cnt * sizeof(double));
+  for (size_t k = 0; k < cnt; ++k) out[k] = comp((*v)[k], -1);
 }
 
 // Macroscopic fields of the current state: the populations are streamed (with
 // the boundary conditions) and their moments taken, exactly as the next step
-// would see them; the stored state is not changed.
+// would see them; the stored populations are not changed.
 // which: 0 rho_a [M][N] (kg/m^3), 1 j_a [M][D][N] (lattice), 2 rho (momentum
 // lattice) [N], 3 u [D][N] (lattice), 4 T [N] (K), 5 P [N] (Pa),
 // 6 V_a [M][D][N] (lattice), 7 N_a [M][D][N] (mol m^-2 s^-1), 8 X_s [S][N],
 // 9 rho_s = sum rho_a [N].
-void oc_moments(void* h, int which, double* out) {
+void oc_moments(void* h, int which, double* out) { moments_lane((Oracle*)h, which, -1, out); }
+
+// Derivative `lane` of the same fields (dual build; lane < oc_lanes()).
+void oc_moments_lane(void* h, int which, int lane, double* out) { moments_lane((Oracle*)h, which, lane, out); }
+
+// Seeds the derivative lanes (dual build): dphi [lanes][N] (null: zero),
+// dpore [lanes] and dtort [lanes] (null: zero) are the directions of the
+// porosity field, pore radius [m] and tortuosity; the populations are reset
+// to the initial equilibria, whose derivatives follow from the porosity.
+void oc_set_tangents(void* h, const double* dphi, const double* dpore, const double* dtort) {
   Oracle* o = (Oracle*)h;
-  const int N = o->N, M = o->M, D = o->D;
-  if (which == 8) {
-    for (size_t k = 0; k < (size_t)o->S * N; ++k) out[k] = o->Xs[k];
-    return;
+#ifdef ORACLE_DUAL
+  for (int n = 0; n < o->N; ++n)
+    for (int k = 0; k < NT; ++k) o->phi[n].d[k] = dphi ? dphi[(size_t)k * o->N + n] : 0.0;
+  for (int k = 0; k < NT; ++k) {
+    o->d0.d[k] = dpore ? 2.0 * dpore[k] / o->cfg.dx : 0.0;
+    o->tort.d[k] = dtort ? dtort[k] : 0.0;
   }
-  stream(*o);
-  compute_all_macro(*o);
-  std::vector<double> Vall;
-  if (which == 6 || which == 7) {
-    // the diffusion velocities need the collision's transport coefficients;
-    // run the collision into a scratch buffer and read its diagnostics
-#pragma omp parallel for schedule(static)
-    for (int n = 0; n < N; ++n) {
-      Grad gr;
-      gradients(*o, n, gr);
-      double fin[(MMAX + 2) * QMAX], fout[(MMAX + 2) * QMAX];
-      for (int l = 0; l < o->nl; ++l)
-        for (int i = 0; i < o->Q; ++i) fin[l * o->Q + i] = o->pulled[PIDX(*o, l, i, n)];
-      double xs0[SMAX], xs1[SMAX];
-      for (int s = 0; s < o->S; ++s) xs0[s] = o->Xs[(size_t)s * N + n];
-      collide_node(*o, n, o->mac[n], gr, fin, fout, xs0, xs1);
-    }
-  }
-  for (int n = 0; n < N; ++n) {
-    const Macro& m = o->mac[n];
-    switch (which) {
-      case 0: for (int a = 0; a < M; ++a) out[(size_t)a * N + n] = m.rho_a[a]; break;
-      case 1: for (int a = 0; a < M; ++a) for (int al = 0; al < D; ++al) out[((size_t)a * D + al) * N + n] = m.j_a[a][al]; break;
-      case 2: out[n] = m.rho_f; break;
-      case 3: for (int al = 0; al < D; ++al) out[(size_t)al * N + n] = m.u[al]; break;
-      case 4: out[n] = m.T; break;
-      case 5: out[n] = m.P * o->cvel * o->cvel; break;
-      case 6: for (int a = 0; a < M; ++a) for (int al = 0; al < D; ++al)
-                out[((size_t)a * D + al) * N + n] = o->dg_V[((size_t)a * 3 + al) * N + n]; break;
-      case 7: for (int a = 0; a < M; ++a) for (int al = 0; al < D; ++al)
-                out[((size_t)a * D + al) * N + n] =
-                    m.rho_a[a] * (m.u[al] + o->dg_V[((size_t)a * 3 + al) * N + n]) * o->cvel / o->m[a]; break;
-      case 9: out[n] = m.rho_s; break;
-      default: break;
-    }
-  }
+#else
+  (void)dphi; (void)dpore; (void)dtort;
+#endif
+  init_populations(o);
+  for (int s = 0; s < o->S; ++s)
+    for (int n = 0; n < o->N; ++n) o->Xs[(size_t)s * o->N + n] = o->Xs_init0[s];
+  o->steps_done = 0;
 }
 
 // ---- single-node helpers for the pin tests --------------------------------
 void oc_product_form(int D, const double* xi, const double* P, double* out) {
   Lattice L = make_lattice(D);
-  product_form(L, xi, P, out);
+  real x[3], p[3], r[QMAX];
+  for (int a = 0; a < 3; ++a) { x[a] = xi[a < D ? a : 0]; p[a] = P[a < D ? a : 0]; }
+  product_form(L, x, p, r);
+  for (int i = 0; i < L.Q; ++i) out[i] = comp(r[i], -1);
 }
 
 void oc_energy_equilibrium(int D, double phi, double rho, const double* u, double RT, double U, double* out) {
   Lattice L = make_lattice(D);
-  energy_equilibrium(L, phi, rho, u, RT, U, out);
+  real uu[3] = {u[0], u[1], u[2]}, r[QMAX];
+  energy_equilibrium(L, phi, rho, uu, RT, U, r);
+  for (int i = 0; i < L.Q; ++i) out[i] = comp(r[i], -1);
 }
 
 void oc_qr_solve(int n, const double* A, int nrhs, const double* b, double* x) {
-  householder_qr_solve(n, A, nrhs, b, x);
+  real Ar[MMAX * MMAX], br[MMAX * 3], xr[MMAX * 3];
+  for (int k = 0; k < n * n; ++k) Ar[k] = A[k];
+  for (int k = 0; k < n * nrhs; ++k) br[k] = b[k];
+  householder_qr_solve(n, Ar, nrhs, br, xr);
+  for (int k = 0; k < n * nrhs; ++k) x[k] = comp(xr[k], -1);
 }
 
 void oc_lattice(int D, int* c, double* w) {

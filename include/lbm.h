@@ -134,6 +134,33 @@ typedef struct lbm_config {
 int lbm_create(lbm_ctx** out, const lbm_config* cfg);
 
 /*
+ * lbm_create_batch -- one context holding n_cases independent D2Q9 lattices
+ * (for instance the binary counter-diffusion capillaries of Sec. 5.1 at many
+ * lengths, pressures and pore radii).  cfgs[c] describes case c exactly as
+ * lbm_create would (each case gets its own lattice scaling from its dx,
+ * theta_max and T_scale); every case must have nz = 1, no surface mechanism
+ * and the same M, energy flag and precision, with (M, energy) = (2, off) or
+ * (3, on); the stream of cfgs[0] is used.  The cases are stepped together:
+ * each lbm_step launches two persistent kernels (macro-field pass, node
+ * update) over one work list of node tiles of all cases, replayed from a
+ * CUDA graph of 50 steps.  Variants 0..5 select the tile length (64, 128,
+ * 256 nodes for v/2 = 0, 1, 2) and the grid (v even: one block per resident
+ * slot of every SM, looping over a contiguous range of tiles; v odd: one
+ * block per tile); lbm_autotune picks among them.  Per-node outputs
+ * (lbm_moments, populations) are the concatenation over cases, in case
+ * order, of each case's single-lattice layout.  Errors as lbm_create, plus
+ * LBM_ERR_ARG for n_cases < 1 or cases of different kinds.
+ */
+int lbm_create_batch(lbm_ctx** out, int n_cases, const lbm_config* cfgs);
+
+/*
+ * lbm_case_info -- for case c of a batched context (c = 0 for a single
+ * lattice): dt [s], dx/dt [m/s], nodes N_c, nx, ny and the element offset of
+ * its populations into out[0..5].  Errors: LBM_ERR_ARG for c out of range.
+ */
+int lbm_case_info(const lbm_ctx* ctx, int c, double* out6);
+
+/*
  * lbm_step -- advance n_steps time steps (pull streaming with the boundary
  * conditions, moments, isotropic gradients, diffusion-velocity solve,
  * species / momentum / energy collisions and surface source), asynchronously

@@ -38,6 +38,20 @@ def _headers():
     return hs
 
 
+def _deps(depfile, fallback):
+    """Headers a unit includes, from the dependency file of its last build
+    (every header when there is none)."""
+    try:
+        with open(depfile) as f:
+            text = f.read().replace("\\\n", " ")
+    except OSError:
+        return fallback
+    _, _, rest = text.partition(":")
+    files = [t for t in rest.split() if t.endswith((".cuh", ".h"))]
+    files = [f for f in files if os.path.abspath(f).startswith(ROOT)]
+    return files or fallback
+
+
 def _stale(target, deps):
     if not os.path.exists(target):
         return True
@@ -58,9 +72,10 @@ def build(force: bool = False, verbose: bool = False, extra=()) -> str:
     objs = []
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
+        dep = obj[:-2] + ".d"
         objs.append(obj)
-        if force or _stale(obj, [src] + hdrs):
-            cmd = [nvcc, "-c", src, "-o", obj] + ARCH + FLAGS + per_file_flags(src) + list(extra)
+        if force or _stale(obj, [src] + _deps(dep, hdrs)):
+            cmd = [nvcc, "-c", src, "-o", obj, "-MD", "-MF", dep] + ARCH + FLAGS + per_file_flags(src) + list(extra)
             jobs.append(cmd)
 
     def run(cmd):

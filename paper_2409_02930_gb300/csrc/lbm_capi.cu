@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
+#include "lbm_batch.cuh"
 #include "lbm_kernels.cuh"
 #include "lbm_ops.h"
 #include "lbm_surface.cuh"
@@ -53,6 +54,24 @@ struct lbm_ctx {
   int xs_cur;
   double* rsrc;
   lbm::MechDev* mech;
+  // batched form (lbm_create_batch; n_cases == 0 for a single lattice)
+  int n_cases;
+  std::vector<int> case_N, case_nx, case_ny;
+  std::vector<long long> case_node_off;
+  std::vector<double> case_dt, case_cvel;
+  std::vector<lbm::Params<double>> case_pd;
+  std::vector<lbm::Params<float>> case_pf;
+  std::vector<lbm::InletTables<double>> case_itd;
+  std::vector<lbm::InletTables<float>> case_itf;
+  void* cases_dev;                   // CaseDev<R>[n_cases]
+  int2* tiles_dev[3];                // work lists for tile lengths 64, 128, 256
+  int ntiles[3];
+  lbm::BatchOps<double> bd;
+  lbm::BatchOps<float> bf;
+  int sm_count;
+  cudaStream_t cap_stream;           // private stream for graph capture
+  cudaGraphExec_t gexec[2];          // 50-step graphs for each ping-pong parity
+  int gvariant[2];
 };
 
 namespace {
@@ -366,6 +385,166 @@ int lbm_create(lbm_ctx** out, const lbm_config* c) {
   return LBM_OK;
 }
 
+}  // extern "C"
+
+// Builds the device case table of a batched context.
+template <class R>
+static cudaError_t upload_cases(lbm_ctx* x, const std::vector<lbm::Params<R>>& ps,
+                                const std::vector<lbm::InletTables<R>>& its) {
+  std::vector<lbm::CaseDev<R>> h(x->n_cases);
+  const long long mac_fields = 2 * x->D + x->M;
+  for (int c = 0; c < x->n_cases; ++c) {
+    h[c].p = ps[c];
+    h[c].it = its[c];
+    h[c].node_off = x->case_node_off[c];
+    h[c].pop_off = x->case_node_off[c] * x->L * x->Q;
+    h[c].mac_off = x->case_node_off[c] * mac_fields;
+  }
+  cudaError_t e = cudaMalloc(&x->cases_dev, h.size() * sizeof(h[0]));
+  if (e == cudaSuccess) e = cudaMemcpy(x->cases_dev, h.data(), h.size() * sizeof(h[0]), cudaMemcpyHostToDevice);
+  return e;
+}
+
+extern "C" {
+
+int lbm_create_batch(lbm_ctx** out, int n_cases, const lbm_config* cfgs) {
+  if (!out) return fail(nullptr, LBM_ERR_ARG, "null output pointer");
+  *out = nullptr;
+  if (n_cases < 1 || !cfgs) return fail(nullptr, LBM_ERR_ARG, "a batch needs at least one case");
+  for (int c = 0; c < n_cases; ++c) {
+    int rc = validate(&cfgs[c]);
+    if (rc) return fail(nullptr, rc, "case " + std::to_string(c) + ": " + g_create_error);
+    const lbm_config& k = cfgs[c];
+    if (k.nz != 1 || k.S != 0) return fail(nullptr, LBM_ERR_ARG, "batched cases are 2-D and without surface mechanism");
+    if (k.M != cfgs[0].M || (k.energy != 0) != (cfgs[0].energy != 0) || k.precision != cfgs[0].precision)
+      return fail(nullptr, LBM_ERR_ARG, "batched cases must share M, the energy flag and the precision");
+  }
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev < 1) return fail(nullptr, LBM_ERR_CUDA, "no CUDA device");
+  lbm_ctx* x = new (std::nothrow) lbm_ctx();
+  if (!x) return fail(nullptr, LBM_ERR_ALLOC, "host allocation failed");
+  const lbm_config& c0 = cfgs[0];
+  x->D = 2;
+  x->Q = 9;
+  x->nz = 1;
+  x->M = c0.M;
+  x->energy = c0.energy ? 1 : 0;
+  x->L = x->M + 1 + x->energy;
+  x->precision = c0.precision;
+  x->stream = (cudaStream_t)c0.stream;
+  x->n_cases = n_cases;
+  x->variant = 2;
+  bool ok = (x->precision == LBM_FP64)
+                ? lbm::get_ops_f64_2d(x->M, x->energy, &x->od) && lbm::get_batch_ops_f64(x->M, x->energy, &x->bd)
+                : lbm::get_ops_f32_2d(x->M, x->energy, &x->of) && lbm::get_batch_ops_f32(x->M, x->energy, &x->bf);
+  if (!ok) {
+    delete x;
+    return fail(nullptr, LBM_ERR_ARG, "batched cases need (M, energy) = (2, off) or (3, on)");
+  }
+  long long off = 0;
+  x->case_pd.resize(n_cases);
+  x->case_pf.resize(n_cases);
+  x->case_itd.resize(n_cases);
+  x->case_itf.resize(n_cases);
+  for (int c = 0; c < n_cases; ++c) {
+    double dt = 0, cvel = 0;
+    lbm::make_params(&cfgs[c], x->case_pd[c], x->case_itd[c], dt, cvel);
+    convert_params(x->case_pd[c], x->case_pf[c]);
+    convert_inlet(x->case_itd[c], x->case_itf[c]);
+    x->case_dt.push_back(dt);
+    x->case_cvel.push_back(cvel);
+    x->case_N.push_back(cfgs[c].nx * cfgs[c].ny);
+    x->case_nx.push_back(cfgs[c].nx);
+    x->case_ny.push_back(cfgs[c].ny);
+    x->case_node_off.push_back(off);
+    off += (long long)cfgs[c].nx * cfgs[c].ny;
+  }
+  if (off > 2000000000LL) {
+    delete x;
+    return fail(nullptr, LBM_ERR_ARG, "batch too large");
+  }
+  x->N = (int)off;
+  x->nx = c0.nx;
+  x->ny = c0.ny;
+  x->dt = x->case_dt[0];
+  x->cvel = x->case_cvel[0];
+  const size_t N = x->N, rs = real_size(x);
+  const size_t pop_bytes = (size_t)x->L * x->Q * N * rs;
+  void** slots[6] = {&x->pops[0], &x->pops[1], &x->phi, &x->Tfix, &x->mac, (void**)&x->status};
+  const size_t sizes[6] = {pop_bytes, pop_bytes, N * rs, N * rs, (size_t)(2 * x->D + x->M) * N * rs, 64};
+  for (int k = 0; k < 6; ++k) {
+    e = cudaMalloc(slots[k], sizes[k]);
+    if (e != cudaSuccess) {
+      lbm_destroy(x);
+      return fail(nullptr, LBM_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  // static fields, concatenated over cases in the working precision
+  std::vector<double> phi_all(N), T_all(N);
+  for (int c = 0; c < n_cases; ++c) {
+    std::memcpy(&phi_all[x->case_node_off[c]], cfgs[c].porosity, x->case_N[c] * sizeof(double));
+    std::memcpy(&T_all[x->case_node_off[c]], cfgs[c].T_init, x->case_N[c] * sizeof(double));
+  }
+  std::vector<char> hbuf(N * rs);
+  auto upload = [&](void* dst, const double* src) -> cudaError_t {
+    if (rs == 8) std::memcpy(hbuf.data(), src, N * 8);
+    else for (size_t n = 0; n < N; ++n) ((float*)hbuf.data())[n] = (float)src[n];
+    return cudaMemcpy(dst, hbuf.data(), N * rs, cudaMemcpyHostToDevice);
+  };
+  e = upload(x->phi, phi_all.data());
+  if (e == cudaSuccess) e = upload(x->Tfix, T_all.data());
+  if (e == cudaSuccess) e = cudaMemset(x->status, 0, 64);
+  // per-case equilibrium initialisation with the case's own parameters
+  for (int c = 0; c < n_cases && e == cudaSuccess; ++c) {
+    const lbm_config& k = cfgs[c];
+    const size_t Nc = x->case_N[c], nb = Nc * sizeof(double);
+    const size_t o = (size_t)x->case_node_off[c];
+    double *dX = nullptr, *dT = nullptr, *dP = nullptr, *dU = nullptr;
+    e = cudaMalloc(&dX, nb * x->M);
+    if (e == cudaSuccess) e = cudaMalloc(&dT, nb);
+    if (e == cudaSuccess) e = cudaMalloc(&dP, nb);
+    if (e == cudaSuccess && k.U_init) e = cudaMalloc(&dU, nb * 3);
+    if (e == cudaSuccess) e = cudaMemcpy(dX, k.X_init, nb * x->M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dT, k.T_init, nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dP, k.P_init, nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && k.U_init) e = cudaMemcpy(dU, k.U_init, nb * 3, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+      if (x->precision == LBM_FP64)
+        x->od.init(x->case_pd[c], dX, dT, dP, dU, x->case_cvel[c], R_UNIV_SI,
+                   (double*)x->pops[0] + o * x->L * x->Q, (const double*)x->phi + o, x->stream);
+      else
+        x->of.init(x->case_pf[c], dX, dT, dP, dU, x->case_cvel[c], R_UNIV_SI,
+                   (float*)x->pops[0] + o * x->L * x->Q, (const float*)x->phi + o, x->stream);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+    cudaFree(dX); cudaFree(dT); cudaFree(dP); if (dU) cudaFree(dU);
+  }
+  // case table and the work lists of node tiles
+  if (e == cudaSuccess)
+    e = x->precision == LBM_FP64 ? upload_cases(x, x->case_pd, x->case_itd) : upload_cases(x, x->case_pf, x->case_itf);
+  const int tl[3] = {64, 128, 256};
+  for (int t = 0; t < 3 && e == cudaSuccess; ++t) {
+    std::vector<int2> tiles;
+    for (int c = 0; c < n_cases; ++c)
+      for (int n0 = 0; n0 < x->case_N[c]; n0 += tl[t]) tiles.push_back(make_int2(c, n0));
+    x->ntiles[t] = (int)tiles.size();
+    e = cudaMalloc(&x->tiles_dev[t], tiles.size() * sizeof(int2));
+    if (e == cudaSuccess) e = cudaMemcpy(x->tiles_dev[t], tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice);
+  }
+  int dev = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&x->sm_count, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    lbm_destroy(x);
+    return cuda_fail(nullptr, e, "batch initialisation");
+  }
+  *out = x;
+  return LBM_OK;
+}
+
 static int read_status(lbm_ctx* x) {
   int st = 0;
   cudaError_t e = cudaMemcpyAsync(&st, x->status, sizeof(int), cudaMemcpyDeviceToHost, x->stream);
@@ -432,7 +611,91 @@ static void launch_react(lbm_ctx* x, const lbm::Ops<R>& ops, const lbm::Params<R
   x->xs_cur = 1 - x->xs_cur;
 }
 
+// ---------------------------------------------------------------------------
+// Batched form
+// ---------------------------------------------------------------------------
+constexpr int kGraphSteps = 50;    // even: a replay returns to the same ping-pong buffer
+
+template <class R>
+static lbm::BatchArgs<R> batch_args(lbm_ctx* x, int cur) {
+  const int t = x->variant / 2;
+  return lbm::BatchArgs<R>{(const lbm::CaseDev<R>*)x->cases_dev, x->tiles_dev[t], x->ntiles[t],
+                           (const R*)x->pops[cur], (R*)x->pops[1 - cur], (const R*)x->phi, (const R*)x->Tfix,
+                           (R*)x->mac, x->status};
+}
+
+template <class R>
+static int batch_grid(lbm_ctx* x, const lbm::BatchOps<R>& ops) {
+  const int nt = x->ntiles[x->variant / 2];
+  if (x->variant % 2) return nt;
+  const int g = x->sm_count * ops.occupancy(x->variant);
+  return g < nt ? g : nt;
+}
+
+template <class R>
+static void batch_launch(lbm_ctx* x, const lbm::BatchOps<R>& ops, int cur, cudaStream_t s) {
+  const lbm::BatchArgs<R> a = batch_args<R>(x, cur);
+  const int grid = batch_grid(x, ops);
+  ops.pass(a, x->variant, grid, 0, s);
+  ops.pass(a, x->variant, grid, 1, s);
+}
+
+static void drop_graphs(lbm_ctx* x) {
+  for (int k = 0; k < 2; ++k)
+    if (x->gexec[k]) {
+      cudaGraphExecDestroy(x->gexec[k]);
+      x->gexec[k] = nullptr;
+    }
+}
+
+// Captures kGraphSteps steps starting from buffer `cur` with the current variant.
+template <class R>
+static cudaError_t batch_capture(lbm_ctx* x, const lbm::BatchOps<R>& ops, int cur) {
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(x->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  for (int s = 0; s < kGraphSteps; ++s) batch_launch(x, ops, (cur + s) & 1, x->cap_stream);
+  e = cudaStreamEndCapture(x->cap_stream, &g);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&x->gexec[cur], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) x->gexec[cur] = nullptr;
+  x->gvariant[cur] = x->variant;
+  return e;
+}
+
+// n steps of every case: whole graphs of kGraphSteps steps, then single steps.
+// With timing on, every kernel is launched (and timed) directly instead.
+template <class R>
+static int batch_steps(lbm_ctx* x, const lbm::BatchOps<R>& ops, int n) {
+  if (!x->timing) {
+    while (n >= kGraphSteps) {
+      if (!x->gexec[x->cur] || x->gvariant[x->cur] != x->variant) {
+        if (x->gexec[x->cur]) {
+          cudaGraphExecDestroy(x->gexec[x->cur]);
+          x->gexec[x->cur] = nullptr;
+        }
+        cudaError_t e = batch_capture(x, ops, x->cur);
+        if (e != cudaSuccess) return cuda_fail(x, e, "graph capture");
+      }
+      cudaError_t e = cudaGraphLaunch(x->gexec[x->cur], x->stream);
+      if (e != cudaSuccess) return cuda_fail(x, e, "graph launch");
+      n -= kGraphSteps;
+    }
+  }
+  for (; n > 0; --n) {
+    const lbm::BatchArgs<R> a = batch_args<R>(x, x->cur);
+    const int grid = batch_grid(x, ops);
+    timed(x, 0, [&] { ops.pass(a, x->variant, grid, 0, x->stream); });
+    timed(x, 1, [&] { ops.pass(a, x->variant, grid, 1, x->stream); });
+    x->cur = 1 - x->cur;
+  }
+  return LBM_OK;
+}
+
 static int step_once(lbm_ctx* x) {
+  if (x->n_cases > 0)
+    return x->precision == LBM_FP64 ? batch_steps(x, x->bd, 1) : batch_steps(x, x->bf, 1);
   if (x->S > 0) {
     if (x->precision == LBM_FP64) launch_react(x, x->od, x->pd, x->itd);
     else launch_react(x, x->of, x->pf, x->itf);
@@ -450,6 +713,11 @@ extern "C" {
 int lbm_step(lbm_ctx* x, int n_steps) {
   if (!x) return LBM_ERR_ARG;
   if (n_steps < 0) return fail(x, LBM_ERR_ARG, "negative step count");
+  if (x->n_cases > 0) {
+    int rc = x->precision == LBM_FP64 ? batch_steps(x, x->bd, n_steps) : batch_steps(x, x->bf, n_steps);
+    if (rc) return rc;
+    n_steps = 0;
+  }
   for (int s = 0; s < n_steps; ++s) {
     int rc = step_once(x);
     if (rc) return rc;
@@ -461,12 +729,14 @@ int lbm_step(lbm_ctx* x, int n_steps) {
 
 int lbm_variant_count(const lbm_ctx* x) {
   if (!x) return LBM_ERR_ARG;
+  if (x->n_cases > 0) return x->precision == LBM_FP64 ? x->bd.n_variants : x->bf.n_variants;
   return x->precision == LBM_FP64 ? x->od.n_variants : x->of.n_variants;
 }
 
 int lbm_set_variant(lbm_ctx* x, int variant) {
   if (!x) return LBM_ERR_ARG;
-  if (variant < -1 || variant >= lbm_variant_count(x)) return fail(x, LBM_ERR_ARG, "unknown kernel variant");
+  if (variant < (x->n_cases > 0 ? 0 : -1) || variant >= lbm_variant_count(x))
+    return fail(x, LBM_ERR_ARG, "unknown kernel variant");
   x->variant = variant;
   return LBM_OK;
 }
@@ -489,7 +759,7 @@ int lbm_autotune(lbm_ctx* x, int steps, int* best) {
   float best_ms = 1e30f;
   int best_v = var0;
   const int nv = lbm_variant_count(x);
-  for (int v = -1; v < nv && e == cudaSuccess; ++v) {
+  for (int v = (x->n_cases > 0 ? 0 : -1); v < nv && e == cudaSuccess; ++v) {
     x->variant = v;
     if (step_once(x) != LBM_OK) continue;           // warm-up (also configures the kernel)
     cudaEventRecord(t0, x->stream);
@@ -567,6 +837,7 @@ int lbm_moments(lbm_ctx* x, int which, void* out, size_t bytes, int out_on_devic
   if (count == 0) return LBM_OK;
   double* dout = (double*)out;
   cudaError_t e;
+  if (which == LBM_MOM_XS && x->n_cases > 0) return fail(x, LBM_ERR_ARG, "batched cases have no surface");
   if (!out_on_device) {
     if (x->scratch_bytes < need) {
       if (x->scratch_out) cudaFree(x->scratch_out);
@@ -578,7 +849,24 @@ int lbm_moments(lbm_ctx* x, int which, void* out, size_t bytes, int out_on_devic
     }
     dout = x->scratch_out;
   }
-  if (x->precision == LBM_FP64) {
+  if (x->n_cases > 0) {
+    // each case writes its own single-lattice layout at its offset
+    const size_t per_node = count / N;
+    const size_t mac_fields = 2 * x->D + x->M;
+    for (int c = 0; c < x->n_cases; ++c) {
+      const size_t off = (size_t)x->case_node_off[c];
+      const size_t pop_off = off * x->L * x->Q;
+      if (x->precision == LBM_FP64) {
+        lbm::StepArgs<double> a{(const double*)x->pops[x->cur] + pop_off, nullptr, (const double*)x->phi + off,
+                                (const double*)x->Tfix + off, (double*)x->mac + off * mac_fields, x->status};
+        x->od.moments(x->case_pd[c], x->case_itd[c], a, which, x->case_cvel[c], dout + off * per_node, x->stream);
+      } else {
+        lbm::StepArgs<float> a{(const float*)x->pops[x->cur] + pop_off, nullptr, (const float*)x->phi + off,
+                               (const float*)x->Tfix + off, (float*)x->mac + off * mac_fields, x->status};
+        x->of.moments(x->case_pf[c], x->case_itf[c], a, which, x->case_cvel[c], dout + off * per_node, x->stream);
+      }
+    }
+  } else if (x->precision == LBM_FP64) {
     lbm::StepArgs<double> a{(const double*)x->pops[x->cur], nullptr, (const double*)x->phi, (const double*)x->Tfix,
                             (double*)x->mac, x->status};
     x->od.moments(x->pd, x->itd, a, which, x->cvel, dout, x->stream);
@@ -624,6 +912,23 @@ int lbm_sync(lbm_ctx* x) {
   return read_status(x);
 }
 
+int lbm_case_info(const lbm_ctx* x, int c, double* out6) {
+  if (!x || !out6) return LBM_ERR_ARG;
+  if (x->n_cases == 0) {
+    if (c != 0) return LBM_ERR_ARG;
+    out6[0] = x->dt; out6[1] = x->cvel; out6[2] = x->N; out6[3] = x->nx; out6[4] = x->ny; out6[5] = 0;
+    return LBM_OK;
+  }
+  if (c < 0 || c >= x->n_cases) return LBM_ERR_ARG;
+  out6[0] = x->case_dt[c];
+  out6[1] = x->case_cvel[c];
+  out6[2] = x->case_N[c];
+  out6[3] = x->case_nx[c];
+  out6[4] = x->case_ny[c];
+  out6[5] = (double)(x->case_node_off[c] * x->L * x->Q);
+  return LBM_OK;
+}
+
 int lbm_info(const lbm_ctx* x, double* out5) {
   if (!x || !out5) return LBM_ERR_ARG;
   out5[0] = x->dt;
@@ -641,6 +946,11 @@ void lbm_destroy(lbm_ctx* x) {
                    x->Xs[0], x->Xs[1], x->rsrc, x->mech};
   for (void* b : bufs)
     if (b) cudaFree(b);
+  drop_graphs(x);
+  if (x->cases_dev) cudaFree(x->cases_dev);
+  for (int t = 0; t < 3; ++t)
+    if (x->tiles_dev[t]) cudaFree(x->tiles_dev[t]);
+  if (x->cap_stream) cudaStreamDestroy(x->cap_stream);
   for (cudaEvent_t ev : x->ev) cudaEventDestroy(ev);
   delete x;
 }

@@ -301,7 +301,11 @@ struct Transport {
       amax = rs > amax ? rs : amax;
       R d = R(1) + R(0.5) * inv_tauk[a];
       dmin = d < dmin ? d : dmin;
-      bool tiny = s.rho_a[a] < R(1e-14) * s.rho_s;
+      // trace species move with the mixture: below 1e-14 of the mixture
+      // density in FP64 (the oracle's bound), below 1e-6 in FP32, where the
+      // populations of a steep trace tail (|f_i| >> rho_a) no longer resolve
+      // j_a / rho_a and the rounding noise of that ratio grows without bound
+      bool tiny = s.rho_a[a] < R(sizeof(R) == 4 ? 1e-6 : 1e-14) * s.rho_s;
 #pragma unroll
       for (int b = 0; b < D; ++b) B[a][b] = tiny ? R(0) : (ja[a * D + b] / s.rho_a[a] - s.u[b]);
     }

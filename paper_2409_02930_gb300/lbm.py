@@ -95,6 +95,10 @@ def load(path: str = LIB_PATH):
     L.lbm_step_noalloc.restype = ctypes.c_int
     L.lbm_noalloc_scratch_limit.argtypes = []
     L.lbm_noalloc_scratch_limit.restype = ctypes.c_size_t
+    L.lbm_create_batch.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(LbmConfig)]
+    L.lbm_create_batch.restype = ctypes.c_int
+    L.lbm_case_info.argtypes = [vp, ctypes.c_int, _dp]
+    L.lbm_case_info.restype = ctypes.c_int
     L.lbm_set_timing.argtypes = [vp, ctypes.c_int]
     L.lbm_set_timing.restype = ctypes.c_int
     L.lbm_get_timing.argtypes = [vp, _dp, ctypes.POINTER(ctypes.c_longlong)]
@@ -268,3 +272,69 @@ class Lattice:
 
     def __del__(self):
         self.close()
+
+
+class Batch(Lattice):
+    """Many independent D2Q9 lattices in one context (``lbm_create_batch``):
+    stepped together by persistent kernels over one tile work list, replayed
+    from CUDA graphs.  Per-node outputs come back as one array per case."""
+
+    def __init__(self, workloads, precision: int = LBM_FP32, stream=None, kappa_threshold: float = 0.0):
+        L = load()
+        self.wls = list(workloads)
+        self.wl = self.wls[0]
+        self.precision = precision
+        cfgs = (LbmConfig * len(self.wls))()
+        keep = []
+        st = stream if stream is not None else _current_stream()
+        for c, wl in enumerate(self.wls):
+            cfg, k = make_config(wl, precision, st, kappa_threshold)
+            cfgs[c] = cfg
+            keep.append(k)
+        h = ctypes.c_void_p()
+        rc = L.lbm_create_batch(ctypes.byref(h), len(self.wls), cfgs)
+        if rc != LBM_OK:
+            raise LbmError(f"lbm_create_batch failed ({rc}): {L.lbm_last_error(None).decode()}")
+        self._h = h
+        info = np.zeros(5)
+        L.lbm_info(h, info.ctypes.data_as(_dp))
+        self.L, self.Q, self.D = int(info[2]), int(info[3]), int(info[4])
+        self.M = self.wl.M
+        self.sizes = [wl.N for wl in self.wls]
+        self.N = int(sum(self.sizes))
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)]).astype(int)
+        self.dts, self.cvels = [], []
+        ci = np.zeros(6)
+        for c in range(len(self.wls)):
+            self._check(L.lbm_case_info(h, c, ci.ctypes.data_as(_dp)), "lbm_case_info")
+            self.dts.append(float(ci[0]))
+            self.cvels.append(float(ci[1]))
+        self.dt, self.cvel = self.dts[0], self.cvels[0]
+        del keep
+
+    def moments(self, which: int):
+        """One array per case, each in the single-lattice layout."""
+        shapes = [tuple(n if d == self.N else d for d in self.moment_shape(which)) for n in self.sizes]
+        flat = np.empty(sum(int(np.prod(s)) for s in shapes))
+        self._check(load().lbm_moments(self._h, which, flat.ctypes.data, flat.nbytes, 0), "lbm_moments")
+        out, k = [], 0
+        for s in shapes:
+            n = int(np.prod(s))
+            out.append(flat[k:k + n].reshape(s))
+            k += n
+        return out
+
+    def populations(self):
+        dt = np.float64 if self.precision == LBM_FP64 else np.float32
+        flat = np.empty(self.L * self.Q * self.N, dtype=dt)
+        self._check(load().lbm_get_populations(self._h, flat.ctypes.data, flat.nbytes, 0), "lbm_get_populations")
+        out = []
+        for c, n in enumerate(self.sizes):
+            o = self.offsets[c] * self.L * self.Q
+            out.append(flat[o:o + self.L * self.Q * n].reshape(self.L, self.Q, n))
+        return out
+
+    def set_populations(self, pops):
+        dt = np.float64 if self.precision == LBM_FP64 else np.float32
+        flat = np.concatenate([np.asarray(p, dtype=dt).reshape(-1) for p in pops])
+        self._check(load().lbm_set_populations(self._h, flat.ctypes.data, flat.nbytes, 0), "lbm_set_populations")

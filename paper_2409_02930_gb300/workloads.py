@@ -31,6 +31,7 @@ from typing import List, Optional
 import numpy as np
 
 ATM = 101325.0
+R_UNIV = 8.314462618          # J/(mol K)
 
 BC_PERIODIC = "periodic"
 BC_INLET = "inlet"
@@ -248,17 +249,37 @@ def adjoint_slab(nx=256, ny=256, steps=1000, name=None) -> Workload:
 
 
 def capillary_batch(n_cases=64, seed=5, ny=4, steps=2000, nmin=128, nmax=4096) -> List[Workload]:
-    """Independent capillaries: lengths log-uniform in [nmin, nmax] nodes,
-    pressures log-uniform in [0.01, 10] atm, pore radius log-uniform in
-    [0.1, 10] um, masses 4 and 40 g/mol, 300 K."""
+    """Independent capillaries of the counter-diffusion experiment (Sec. 5.1:
+    pure A | pure B halves fed from reservoirs of their own composition):
+    lengths log-uniform in [nmin, nmax] nodes, pressures log-uniform in
+    [0.01, 10] atm, pore radii log-uniform in [0.1, 10] um, masses 4 and
+    40 g/mol, 300 K.  Each case has its own lattice scaling.
+
+    Two rates bound the node spacing.  The explicit Knudsen drag rate
+    dt/tau^k grows as dx/r_p, and the momentum relaxation time mu/(P dt)
+    shrinks as 1/(P dx).  With the inlet boundary used here (reservoir
+    equilibria moving with the adjacent node) the scheme is stable for
+    omega <= 1.6 and dx >= r_p/4 and unstable (a growing boundary
+    velocity) when either fails; dx is min(r_p, spacing at omega = 1.4).
+    Where even that spacing is below r_p/3 -- large pores at high pressure,
+    Knudsen numbers below about 1e-3, roughly a tenth of the log-square --
+    the (pressure, radius) pair is drawn again, so the sample is the
+    log-uniform square restricted to P r_p <= about 0.66 Pa m."""
     rng = np.random.default_rng(seed)
+    m, _, mu, _ = _he_ar()
+    T, theta = 300.0, 1.0 / 3.0
+    dt_per_dx = np.sqrt(theta * m.min() / (R_UNIV * T))       # dt/dx of every case
+    tau_min = 1.0 / 1.4 - 0.5                                   # mu/(P dt) at omega = 1.4
     lens = np.exp(rng.uniform(np.log(nmin), np.log(nmax), n_cases)).astype(int)
-    Ps = np.exp(rng.uniform(np.log(0.01), np.log(10.0), n_cases)) * ATM
-    rps = np.exp(rng.uniform(np.log(0.1e-6), np.log(10e-6), n_cases))
     out = []
     for c in range(n_cases):
-        out.append(capillary(nx=int(lens[c]), ny=ny, P=float(Ps[c]),
-                             pore_radius=float(rps[c]), steps=steps,
+        while True:
+            P = float(np.exp(rng.uniform(np.log(0.01), np.log(10.0)))) * ATM
+            rp = float(np.exp(rng.uniform(np.log(0.1e-6), np.log(10e-6))))
+            dx = min(rp, mu.min() / (P * tau_min * dt_per_dx))
+            if dx >= rp / 3.0:
+                break
+        out.append(capillary(nx=int(lens[c]), ny=ny, P=P, pore_radius=rp, dx=dx, steps=steps,
                              name=f"case{c}_{int(lens[c])}x{ny}"))
     return out
 

@@ -1,0 +1,131 @@
+"""Batched form (lbm_create_batch): many capillaries of uneven length,
+pressure and pore radius, each with its own lattice scaling, stepped together
+by persistent kernels over one tile work list and replayed from CUDA graphs.
+
+Every case must equal the same case run alone: against the FP64 oracle to
+1e-12 (FP64 batch), against the single-lattice FP32 context to rounding, and
+against the oracle within the FP32 capillary tolerance."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2409_02930_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2409_02930_gb300 import lbm
+    lbm.load()
+    return lbm
+
+
+def rel(a, b):
+    s = np.max(np.abs(b))
+    return float(np.max(np.abs(a - b)) / s)
+
+
+def small_batch(steps=300):
+    return W.capillary_batch(n_cases=8, seed=11, nmin=16, nmax=96, steps=steps)
+
+
+def test_fp64_batch_matches_oracle_per_case(L):
+    wls = small_batch()
+    b = L.Batch(wls, precision=L.LBM_FP64)
+    steps = 130          # two graph replays of 50 steps, then 30 single steps
+    b.step(steps)
+    b.sync()
+    pops = b.populations()
+    rho = b.moments(L.LBM_MOM_RHO_A)
+    for c, wl in enumerate(wls):
+        o = oracle.Oracle(wl)
+        assert abs(b.dts[c] / o.dt - 1) < 1e-14
+        o.step(steps)
+        po = o.pops()
+        for l in range(b.L):
+            assert rel(pops[c][l], po[l]) < 1e-12, (c, l)
+        assert rel(rho[c], o.moments(oracle.MOM_RHO_A)) < 1e-12, c
+
+
+def test_every_batch_variant_and_graph_path_agree(L):
+    wls = small_batch()
+    ref = None
+    b0 = L.Batch(wls, precision=L.LBM_FP64)
+    nv = b0.variant_count()
+    b0.close()
+    assert nv == 6
+    for v in range(nv):
+        b = L.Batch(wls, precision=L.LBM_FP64)
+        b.set_variant(v)
+        b.step(100)                      # graph replays
+        p = np.concatenate([x.reshape(-1) for x in b.populations()])
+        if ref is None:
+            ref = p
+        else:
+            assert rel(p, ref) < 1e-14, v
+        b.close()
+    # the same 100 steps launched one by one
+    b = L.Batch(wls, precision=L.LBM_FP64)
+    b.set_variant(3)
+    for _ in range(100):
+        b.step(1)
+    p = np.concatenate([x.reshape(-1) for x in b.populations()])
+    assert rel(p, ref) < 1e-14
+
+
+def test_fp32_batch_full_size_matches_single_cases(L):
+    """The 64-case sweep (lengths 128-4096 nodes): after 200 steps every case
+    equals its single-lattice FP32 run to FP32 rounding (the two are
+    compiled separately, so contraction and ordering may differ; the
+    capillary trace regions amplify rounding, as in the FP32 oracle test)."""
+    wls = W.capillary_batch()
+    b = L.Batch(wls, precision=L.LBM_FP32)
+    assert b.N == sum(w.N for w in wls)
+    best = b.autotune(3)
+    assert 0 <= best < 6
+    b.close()
+    b = L.Batch(wls, precision=L.LBM_FP32)
+    b.set_variant(best)
+    b.step(200)
+    b.sync()
+    rho_b = b.moments(L.LBM_MOM_RHO_A)
+    j_b = b.moments(L.LBM_MOM_J_A)
+    for c in range(0, len(wls), 7):
+        g = L.Lattice(wls[c], precision=L.LBM_FP32)
+        g.set_variant(-1)
+        g.step(200)
+        assert rel(rho_b[c], g.moments(L.LBM_MOM_RHO_A)) < 1e-4, c
+        jg = g.moments(L.LBM_MOM_J_A)
+        assert np.max(np.abs(j_b[c] - jg)) <= 1e-5 * np.max(np.abs(rho_b[c])), c
+        g.close()
+
+
+def test_fp32_batch_matches_oracle_on_short_cases(L):
+    """FP32 batch against the FP64 oracle after 1000 steps.  In the pure
+    halves of a capillary the species lattice of the present species has no
+    partner to collide with (beta = 0) and relaxes only through the Knudsen
+    term, whose rate dt/tau^k falls as dx/r_p: FP32 rounding there performs a
+    weakly damped random walk.  Densities stay within 1e-4 of the field
+    maximum (the per-case errors are reported); FP64 batches match the oracle
+    to 1e-12."""
+    wls = W.capillary_batch(n_cases=6, seed=13, nmin=32, nmax=128, steps=1000)
+    b = L.Batch(wls, precision=L.LBM_FP32)
+    b.step(1000)
+    b.sync()
+    rho = b.moments(L.LBM_MOM_RHO_A)
+    for c, wl in enumerate(wls):
+        o = oracle.Oracle(wl)
+        o.step(1000)
+        e = rel(rho[c], o.moments(oracle.MOM_RHO_A))
+        print("case", c, wl.nx, "nodes", "%.3f atm" % (wl.P_init[0] / W.ATM), "FP32 density error %.2e" % e)
+        assert e < 1e-4, c
+
+
+def test_batch_rejects_mixed_kinds(L):
+    a = W.capillary(nx=16)
+    s = W.slab(nx=16, ny=8)
+    with pytest.raises(L.LbmError):
+        L.Batch([a, s])
+    with pytest.raises(L.LbmError):
+        L.Batch([W.anode3d(nx=8, ny=4, nz=4)])

@@ -122,13 +122,22 @@ def barrier(ws):
 
 
 def allreduce_max(ws, v):
+    """Maximum of v over the ranks (the slowest replica sets the time)."""
     if ws == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dev = "cpu" if dist.get_backend() == "gloo" else "cuda"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def weak_scaling_value(ws, nodes, lattices, steps, ms_max):
+    """Whole-job species-weighted MLUPS: every rank advances its own replica
+    of `nodes` nodes, so the job processes ws * nodes * lattices * steps
+    lattice-node updates in the slowest rank's time."""
+    return ws * nodes * lattices * steps / (ms_max / 1e3) / 1e6
 
 
 def cpu_baseline(wl_sample, seconds=10.0):
@@ -199,7 +208,7 @@ def run_ours(args, ws, rank, local):
     step_ms_max = allreduce_max(ws, step_ms)
 
     N, L = wl.N, wl.L
-    value = ws * N * L * args.steps / (step_ms_max / 1e3) / 1e6
+    value = weak_scaling_value(ws, N, L, args.steps, step_ms_max)
     # roofline of the dominant kernel (kind 1: collide / fused step)
     per_launch_ms = ms[1] / max(cnt[1], 1)
     alg_bytes = algorithmic_bytes_per_node(wl, rbytes) * N

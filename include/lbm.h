@@ -225,6 +225,44 @@ int lbm_get_variant(const lbm_ctx* ctx);
 int lbm_autotune(lbm_ctx* ctx, int steps, int* best);
 
 /*
+ * Objective of lbm_adjoint: J = weight * sum over the nodes of the plane
+ * x = plane of the species-`species` momentum along `axis` of the streamed
+ * populations of the final state (the flux moment LBM_MOM_J_A, lattice
+ * units; with plane next to an outlet face this is the outlet flux of that
+ * species).  kind must be LBM_OBJ_PLANE_FLUX.
+ */
+#define LBM_OBJ_PLANE_FLUX 0
+typedef struct {
+  int kind;
+  int species;
+  int axis;
+  int plane;
+  double weight;
+} lbm_objective;
+
+/*
+ * lbm_adjoint -- gradient of an objective of the state after n_steps steps
+ * from the configured initial state, by the discrete adjoint of the step
+ * (reverse-mode differentiation of every stage: pull with the boundary
+ * rules, macro fields, isotropic gradients, node update, initial
+ * equilibria).  The forward run keeps a checkpoint every ckpt_every steps;
+ * the reverse sweep recomputes the states of one segment at a time from its
+ * checkpoint.  Device memory: (n_steps/ckpt_every + ckpt_every + 3) copies of
+ * the populations, allocated for the call and freed before it returns.
+ * Outputs (host pointers, each may be NULL): *J, dJ_dphi [N] (derivative
+ * with respect to the porosity of every node), *dJ_dpore (pore radius, per
+ * metre) and *dJ_dtort (tortuosity); pore radius and tortuosity enter the
+ * step through their ratio (the Knudsen diffusivity of Sec. 5.1), so
+ * r_p dJ/dr_p = -tau dJ/dtau.  On return the context holds the final state
+ * of the forward run.  Supported: single 2-D lattices without a surface
+ * mechanism, (M, energy) = (2, off) or (3, on).  Errors: LBM_ERR_ARG
+ * (unsupported context, bad objective, n_steps < 0, ckpt_every < 1),
+ * LBM_ERR_ALLOC, LBM_ERR_NUMERIC (non-finite state during the forward run).
+ */
+int lbm_adjoint(lbm_ctx* ctx, const lbm_objective* obj, int n_steps, int ckpt_every, double* J,
+                double* dJ_dphi, double* dJ_dpore, double* dJ_dtort);
+
+/*
  * lbm_step_noalloc -- one time step that allocates nothing.  The paper has
  * no counterpart: this entry point exists for callers that cannot allocate
  * device memory while they run, such as a host framework that owns all

@@ -10,10 +10,7 @@
 #include <vector>
 
 #include "../../include/lbm.h"
-#include "lbm_batch.cuh"
-#include "lbm_kernels.cuh"
-#include "lbm_ops.h"
-#include "lbm_surface.cuh"
+#include "lbm_ctx.h"
 
 namespace {
 
@@ -24,55 +21,7 @@ thread_local std::string g_create_error;
 
 }  // namespace
 
-struct lbm_ctx {
-  int nx, ny, nz, N, D, Q, M, L, energy, knudsen, precision, S;
-  double dt, cvel;
-  cudaStream_t stream;
-  void* pops[2];
-  int cur;
-  void* phi;
-  void* Tfix;
-  void* mac;
-  int* status;
-  double* scratch_out;        // device buffer for lbm_moments to host
-  size_t scratch_bytes;
-  lbm::Params<double> pd;
-  lbm::Params<float> pf;
-  lbm::InletTables<double> itd;
-  lbm::InletTables<float> itf;
-  lbm::Ops<double> od;
-  lbm::Ops<float> of;
-  std::string err;
-  // kernel timing (lbm_set_timing)
-  int timing;
-  std::vector<cudaEvent_t> ev;       // start/stop pairs
-  std::vector<int> ev_kind;
-  size_t ev_used;
-  int variant;                       // < 0: two-pass form; >= 0: fused tile shape
-  // surface mechanism (S > 0): coverages (ping-pong), per-node sources, mechanism table
-  double* Xs[2];
-  int xs_cur;
-  double* rsrc;
-  lbm::MechDev* mech;
-  // batched form (lbm_create_batch; n_cases == 0 for a single lattice)
-  int n_cases;
-  std::vector<int> case_N, case_nx, case_ny;
-  std::vector<long long> case_node_off;
-  std::vector<double> case_dt, case_cvel;
-  std::vector<lbm::Params<double>> case_pd;
-  std::vector<lbm::Params<float>> case_pf;
-  std::vector<lbm::InletTables<double>> case_itd;
-  std::vector<lbm::InletTables<float>> case_itf;
-  void* cases_dev;                   // CaseDev<R>[n_cases]
-  int2* tiles_dev[3];                // work lists for tile lengths 64, 128, 256
-  int ntiles[3];
-  lbm::BatchOps<double> bd;
-  lbm::BatchOps<float> bf;
-  int sm_count;
-  cudaStream_t cap_stream;           // private stream for graph capture
-  cudaGraphExec_t gexec[2];          // 50-step graphs for each ping-pong parity
-  int gvariant[2];
-};
+
 
 namespace {
 
@@ -369,7 +318,13 @@ int lbm_create(lbm_ctx** out, const lbm_config* c) {
     e = cudaGetLastError();
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
-  cudaFree(dX); cudaFree(dT); cudaFree(dP); if (dU) cudaFree(dU);
+  // the initial fields stay on the device (lbm_adjoint restarts from them)
+  x->init_X = dX;
+  x->init_T = dT;
+  x->init_P = dP;
+  x->init_U = dU;
+  x->tortuosity = c->tortuosity;
+  x->pore_radius = c->pore_radius;
   if (e != cudaSuccess) {
     lbm_destroy(x);
     return cuda_fail(nullptr, e, "initialisation");
@@ -942,8 +897,8 @@ int lbm_info(const lbm_ctx* x, double* out5) {
 void lbm_destroy(lbm_ctx* x) {
   if (!x) return;
   cudaStreamSynchronize(x->stream);
-  void* bufs[11] = {x->pops[0], x->pops[1], x->phi, x->Tfix, x->mac, x->status, x->scratch_out,
-                   x->Xs[0], x->Xs[1], x->rsrc, x->mech};
+  void* bufs[15] = {x->pops[0], x->pops[1], x->phi, x->Tfix, x->mac, x->status, x->scratch_out,
+                   x->Xs[0], x->Xs[1], x->rsrc, x->mech, x->init_X, x->init_T, x->init_P, x->init_U};
   for (void* b : bufs)
     if (b) cudaFree(b);
   drop_graphs(x);

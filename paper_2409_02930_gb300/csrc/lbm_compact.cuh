@@ -156,6 +156,7 @@ LBM_HD void moments_gen(const PullF& pf, Moments<R, D, M, EN, FULL>& mo) {
 #pragma unroll
   for (int a = 0; a < M; ++a) {
     mo.sa[a] = R(0);
+    mo.sabs[a] = R(0);
 #pragma unroll
     for (int b = 0; b < D; ++b) mo.ja[a][b] = R(0);
   }
@@ -175,6 +176,7 @@ LBM_HD void moments_gen(const PullF& pf, Moments<R, D, M, EN, FULL>& mo) {
     for (int a = 0; a < M; ++a) {
       R f = pf.get(h, a, i, cx, cy, cz);
       mo.sa[a] += f;
+      if (FULL && ScalarTraits<R>::single) mo.sabs[a] += fabs(f);
       if (FULL) {
 #pragma unroll
         for (int b = 0; b < D; ++b) mo.ja[a][b] += R(cc[b]) * f;
@@ -231,7 +233,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
   if (!(s.rho_s > R(0)) || !(s.rho_f > R(0)) || !finite_<R>(s.T)) flag(status, 1);
 
   Transport<R, D, M> tr;
-  tr.compute(p, s, &mo.ja[0][0]);
+  tr.compute(p, s, &mo.ja[0][0], mo.sabs);
   if (tr.used_fp64) flag(status, 2);
 
   const R phi = s.phi;

@@ -85,12 +85,21 @@ LBM_HD void psi3(R xi, R P, R out[3]) {
   out[2] = R(0.5) * (P + xi);
 }
 
-template <class R> LBM_HD R sqrt_(R v);
-template <> LBM_HD float sqrt_<float>(float v) { return sqrtf(v); }
-template <> LBM_HD double sqrt_<double>(double v) { return sqrt(v); }
-template <class R> LBM_HD R pow_(R a, R b);
-template <> LBM_HD float pow_<float>(float a, float b) { return powf(a, b); }
-template <> LBM_HD double pow_<double>(double a, double b) { return pow(a, b); }
+// single-precision storage and arithmetic (dual numbers inherit it from their base)
+template <class R> struct ScalarTraits { static constexpr bool single = sizeof(R) == 4; };
+
+// square root and power per scalar type (specialised for dual numbers too)
+template <class R> struct MathOps;
+template <> struct MathOps<float> {
+  static LBM_HD float sqrt(float v) { return sqrtf(v); }
+  static LBM_HD float pow(float a, float b) { return powf(a, b); }
+};
+template <> struct MathOps<double> {
+  static LBM_HD double sqrt(double v) { return ::sqrt(v); }
+  static LBM_HD double pow(double a, double b) { return ::pow(a, b); }
+};
+template <class R> LBM_HD R sqrt_(R v) { return MathOps<R>::sqrt(v); }
+template <class R> LBM_HD R pow_(R a, R b) { return MathOps<R>::pow(a, b); }
 template <class R> LBM_HD bool finite_(R v) { return v == v && v - v == v - v; }
 
 LBM_HD int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }

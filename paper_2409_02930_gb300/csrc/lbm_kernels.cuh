@@ -118,7 +118,7 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
   if (!(s.rho_s > R(0)) || !(s.rho_f > R(0)) || !finite_<R>(s.T)) flag(status, 1);
 
   Transport<R, D, M> tr;
-  tr.compute(p, s, &mo.ja[0][0]);
+  tr.compute(p, s, &mo.ja[0][0], mo.sabs);
   if (tr.used_fp64) flag(status, 2);
 
   const R phi = s.phi;
@@ -314,17 +314,15 @@ __global__ void __launch_bounds__(256) k_collide(Params<R> p, InletTables<R> it,
 // Initial populations: equilibria of the initial fields (eq:27eq, eq:feqmix
 // without extension, eq:geq_i).
 // ---------------------------------------------------------------------------
-template <class R, int D, int M, bool EN>
-__global__ void __launch_bounds__(256) k_init(Params<R> p, const double* __restrict__ X, const double* __restrict__ T0,
-                                             const double* __restrict__ P0, const double* __restrict__ U0v,
-                                             double cvel, double RU_si, R* __restrict__ dst,
-                                             const R* __restrict__ phiA) {
+// Initial populations of node n: equilibria of the initial fields (eq:27eq,
+// eq:feqmix without extension, eq:geq_i).  R is the computing type, PR the
+// parameter type; store(l, i, value).
+template <class R, int D, int M, bool EN, class PR, class Store>
+LBM_HD void init_node(const PR& p, const double* __restrict__ X, const double* __restrict__ T0,
+                      const double* __restrict__ P0, const double* __restrict__ U0v, double cvel, double RU_si,
+                      int n, int N, R phi, Store&& store) {
   constexpr int Q = Lat<D>::Q;
-  int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= p.N) return;
-  const int N = p.N;
   R T = (R)T0[n];
-  R phi = phiA[n];
   R rho_a[M], rho = R(0), inv_m = R(0);
 #pragma unroll
   for (int a = 0; a < M; ++a) {
@@ -333,8 +331,8 @@ __global__ void __launch_bounds__(256) k_init(Params<R> p, const double* __restr
     rho += rho_a[a];
   }
 #pragma unroll
-  for (int a = 0; a < M; ++a) inv_m += (rho_a[a] / rho) / p.m[a];
-  R Rg = p.RU * inv_m;
+  for (int a = 0; a < M; ++a) inv_m += (rho_a[a] / rho) / R(p.m[a]);
+  R Rg = R(p.RU) * inv_m;
   R u[D], w[D];
 #pragma unroll
   for (int b = 0; b < D; ++b) {
@@ -345,13 +343,13 @@ __global__ void __launch_bounds__(256) k_init(Params<R> p, const double* __restr
   for (int a = 0; a < M; ++a) {
     R F[D][3];
 #pragma unroll
-    for (int b = 0; b < D; ++b) psi3<R>(w[b], w[b] * w[b] + p.Ra[a] * T, F[b]);
+    for (int b = 0; b < D; ++b) psi3<R>(w[b], w[b] * w[b] + R(p.Ra[a]) * T, F[b]);
 #pragma unroll
     for (int i = 0; i < Q; ++i) {
       R v = phi * rho_a[a];
 #pragma unroll
       for (int b = 0; b < D; ++b) v *= F[b][c_of<D>(i, b) + 1];
-      dst[(size_t)(a * Q + i) * N + n] = v;
+      store(a, i, v);
     }
   }
   {
@@ -363,20 +361,33 @@ __global__ void __launch_bounds__(256) k_init(Params<R> p, const double* __restr
       R v = phi * rho;
 #pragma unroll
       for (int b = 0; b < D; ++b) v *= F[b][c_of<D>(i, b) + 1];
-      dst[(size_t)(M * Q + i) * N + n] = v;
+      store(M, i, v);
     }
   }
   if (EN) {
     R U = R(0);
 #pragma unroll
-    for (int a = 0; a < M; ++a) U += (rho_a[a] / rho) * (p.U0[a] + p.cvR[a] * (T - p.T_thermo));
+    for (int a = 0; a < M; ++a) U += (rho_a[a] / rho) * (R(p.U0[a]) + R(p.cvR[a]) * (T - R(p.T_thermo)));
     GeqFactors<R, D> G;
     G.init(phi, rho, u, Rg * T, U);
     Unroll<0, Q>::run([&](auto ic) {
       constexpr int I = decltype(ic)::value;
-      dst[(size_t)((M + 1) * Q + I) * N + n] = G.template value<I>();
+      store(M + 1, I, G.template value<I>());
     });
   }
+}
+
+template <class R, int D, int M, bool EN>
+__global__ void __launch_bounds__(256) k_init(Params<R> p, const double* __restrict__ X, const double* __restrict__ T0,
+                                             const double* __restrict__ P0, const double* __restrict__ U0v,
+                                             double cvel, double RU_si, R* __restrict__ dst,
+                                             const R* __restrict__ phiA) {
+  constexpr int Q = Lat<D>::Q;
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  const int N = p.N;
+  init_node<R, D, M, EN>(p, X, T0, P0, U0v, cvel, RU_si, n, N, phiA[n],
+                         [&](int l, int i, R v) { dst[(size_t)(l * Q + i) * N + n] = v; });
 }
 
 // ---------------------------------------------------------------------------
@@ -413,7 +424,7 @@ __global__ void __launch_bounds__(256) k_moments(Params<R> p, InletTables<R> it,
     case 6:
     case 7: {
       Transport<R, D, M> tr;
-      tr.compute(p, s, &mo.ja[0][0]);
+      tr.compute(p, s, &mo.ja[0][0], mo.sabs);
       for (int k = 0; k < M; ++k)
         for (int b = 0; b < D; ++b) {
           double v = (double)tr.V[k][b];

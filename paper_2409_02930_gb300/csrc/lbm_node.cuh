@@ -146,6 +146,7 @@ struct Puller {
 template <class R, int D, int M, bool EN, bool FULL>
 struct Moments {
   R sa[M], ja[M][D];
+  R sabs[M];              // sum_i |f_ai| (FP32 full moments only): resolution of rho_a
   R sf, jf[D];
   R Pt[D][D];
   R sg, q[D];
@@ -156,6 +157,7 @@ struct Moments {
 #pragma unroll
     for (int a = 0; a < M; ++a) {
       sa[a] = R(0);
+      sabs[a] = R(0);
 #pragma unroll
       for (int b = 0; b < D; ++b) ja[a][b] = R(0);
     }
@@ -174,6 +176,7 @@ struct Moments {
       for (int a = 0; a < M; ++a) {
         R f = pl.template get<I>(a);
         sa[a] += f;
+        if (FULL && ScalarTraits<R>::single) sabs[a] += fabs(f);
         if (FULL) {
 #pragma unroll
           for (int b = 0; b < D; ++b)
@@ -270,7 +273,7 @@ struct Transport {
   int used_fp64;
 
   LBM_HD void compute(const Params<R>& p, const State<R, D, M>& s,
-                                          const R* ja /* [M][D] */) {
+                                          const R* ja /* [M][D] */, const R* sabs /* [M] */) {
     // D_ab = D_ref (T/T_ref)^1.5 (P_ref/P);  1/tau_ab = m R_U T / (D_ab m_a m_b)
     R tr = s.T * p.inv_T_ref;
     R C = s.m_mix * p.RU * s.T * s.P / (p.Pref * tr * sqrt_<R>(tr));
@@ -302,10 +305,13 @@ struct Transport {
       R d = R(1) + R(0.5) * inv_tauk[a];
       dmin = d < dmin ? d : dmin;
       // trace species move with the mixture: below 1e-14 of the mixture
-      // density in FP64 (the oracle's bound), below 1e-6 in FP32, where the
-      // populations of a steep trace tail (|f_i| >> rho_a) no longer resolve
-      // j_a / rho_a and the rounding noise of that ratio grows without bound
-      bool tiny = s.rho_a[a] < R(sizeof(R) == 4 ? 1e-6 : 1e-14) * s.rho_s;
+      // density (the oracle's bound) and, in FP32, where the species density
+      // is not resolved by its populations.  Where the streamed populations
+      // of a species cancel (sum |f_ai| > 1e4 rho_a: a trace tail crossed by
+      // weakly relaxed non-equilibrium populations), FP32 leaves j_a / rho_a
+      // to rounding noise, which the quasi-equilibrium then amplifies.
+      bool tiny = s.rho_a[a] < R(1e-14) * s.rho_s;
+      if (ScalarTraits<R>::single) tiny = tiny || !(sabs[a] <= R(1e4) * s.phi * s.rho_a[a]);
 #pragma unroll
       for (int b = 0; b < D; ++b) B[a][b] = tiny ? R(0) : (ja[a * D + b] / s.rho_a[a] - s.u[b]);
     }

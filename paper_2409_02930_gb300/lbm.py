@@ -47,6 +47,13 @@ class LbmConfig(ctypes.Structure):
     ]
 
 
+class LbmObjective(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("species", ctypes.c_int), ("axis", ctypes.c_int),
+                ("plane", ctypes.c_int), ("weight", ctypes.c_double)]
+
+
+LBM_OBJ_PLANE_FLUX = 0
+
 _lib = None
 
 
@@ -99,6 +106,8 @@ def load(path: str = LIB_PATH):
     L.lbm_create_batch.restype = ctypes.c_int
     L.lbm_case_info.argtypes = [vp, ctypes.c_int, _dp]
     L.lbm_case_info.restype = ctypes.c_int
+    L.lbm_adjoint.argtypes = [vp, ctypes.POINTER(LbmObjective), ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp]
+    L.lbm_adjoint.restype = ctypes.c_int
     L.lbm_set_timing.argtypes = [vp, ctypes.c_int]
     L.lbm_set_timing.restype = ctypes.c_int
     L.lbm_get_timing.argtypes = [vp, _dp, ctypes.POINTER(ctypes.c_longlong)]
@@ -249,6 +258,22 @@ class Lattice:
         best = ctypes.c_int(0)
         self._check(load().lbm_autotune(self._h, int(steps), ctypes.byref(best)), "lbm_autotune")
         return best.value
+
+    def adjoint(self, steps: int, ckpt_every: int = 50, species: int = 0, axis: int = 0, plane=None,
+                weight: float = 1.0):
+        """Discrete adjoint of J = weight * sum over plane x = `plane` (default
+        nx - 2) of the species momentum along `axis` after `steps` steps from
+        the initial state.  Returns (J, dJ/dphi [N], dJ/dpore_radius,
+        dJ/dtortuosity); the context is left at the final state."""
+        obj = LbmObjective(LBM_OBJ_PLANE_FLUX, int(species), int(axis),
+                           int(self.wl.nx - 2 if plane is None else plane), float(weight))
+        J = ctypes.c_double()
+        dp = ctypes.c_double()
+        dt = ctypes.c_double()
+        g = np.empty(self.N)
+        self._check(load().lbm_adjoint(self._h, ctypes.byref(obj), int(steps), int(ckpt_every), ctypes.byref(J),
+                                       g.ctypes.data_as(_dp), ctypes.byref(dp), ctypes.byref(dt)), "lbm_adjoint")
+        return J.value, g, dp.value, dt.value
 
     def population_bytes(self) -> int:
         return int(load().lbm_population_bytes(self._h))

@@ -114,7 +114,7 @@ def test_fp32_adjoint_matches_fp64_adjoint_small(L):
     e = np.max(np.abs(b[1] - a[1])) / np.max(np.abs(a[1]))
     print("FP32 vs FP64 adjoint gradient: %.2e" % e)
     assert abs(b[0] - a[0]) <= 1e-4 * abs(a[0])
-    assert e < 1e-3
+    assert e < 1e-4            # measured 2.0e-6
 
 
 def test_autograd_function(L):
@@ -167,5 +167,5 @@ def test_full_size_adjoint_against_central_differences(L):
     e64 = np.max(np.abs(a64 - fd)) / scale
     e32 = np.max(np.abs(a32 - fd)) / scale
     print("full size: J64 %.6e J32 %.6e; adjoint vs central differences: FP64 %.2e FP32 %.2e" % (J64, J32, e64, e32))
-    assert e64 < 1e-5
-    assert e32 < 1e-2
+    assert e64 < 1e-6          # measured 3.0e-9 (central-difference truncation)
+    assert e32 < 1e-4          # measured 2.0e-6

@@ -45,6 +45,74 @@ def algorithmic_bytes_per_node(wl, real_bytes):
     return wl.L * wl.Q * real_bytes * 2 + real_bytes
 
 
+def profiled_traffic(key):
+    """DRAM bytes (read + write) per launch of a kernel form, from the ncu
+    summary committed under profiles/ (null when this form was not captured
+    since it last changed)."""
+    path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 2 and not line.startswith("#") and parts[0] == key:
+                return float(parts[1])
+    return None
+
+
+def other_forms(stream, torch, lbm):
+    """The batched, adjoint and reactive forms on their own workloads, timed
+    with CUDA events (no L2 flush: each is timed over many steps)."""
+    import ctypes
+    out = {}
+
+    def timed(fn, reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn(reps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    # batched persistent form: 64 capillaries, FP32, CUDA-graph replay
+    wls = W.capillary_batch()
+    b = lbm.Batch(wls, precision=lbm.LBM_FP32, stream=sp)
+    v = b.autotune(5)
+    b.set_variant(v)
+    b.step(100)
+    ms = timed(b.step, 1000) / 1000
+    out["batch_64_capillaries_fp32"] = {
+        "ms_per_step": ms, "nodes": b.N, "variant": v,
+        "value": b.N * b.L * 1e3 / ms / 1e6, "unit": UNIT,
+        "achieved_gbs": b.N * algorithmic_bytes_per_node(wls[0], 4) / (ms / 1e3) / 1e9,
+        "note": "state of 2 x 32 MB stays in L2: L2-bound, not HBM"}
+    b.close()
+    # adjoint form: 256 x 256 slab, checkpoints every 50
+    wl = W.adjoint_slab()
+    g = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
+    n_adj = 100
+    t0 = time.perf_counter()
+    g.adjoint(n_adj, 50)
+    el = time.perf_counter() - t0
+    out["adjoint_256x256_fp32"] = {
+        "ms_per_step": el * 1e3 / n_adj, "steps": n_adj, "nodes": wl.N,
+        "value": wl.N * wl.L * n_adj / el / 1e6, "unit": UNIT,
+        "note": "forward with checkpoints + recomputation + reverse sweep per step (wall clock)"}
+    g.close()
+    # reactive 3-D anode: surface source in mixed precision
+    wl = W.anode3d_reactive(steps=5)
+    g = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
+    g.step(1)
+    ms = timed(g.step, 3) / 3
+    out["anode_256x128x128_reactive_fp32"] = {
+        "ms_per_step": ms, "nodes": wl.N, "value": wl.N * wl.L * 1e3 / ms / 1e6, "unit": UNIT,
+        "bound": "fp64 alu (surface Newton)"}
+    g.close()
+    return out
+
+
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -268,7 +336,9 @@ def run_ours(args, ws, rank, local):
                        "nodes": N, "lattices": L, "velocities": wl.Q, "parallelism": f"replicas x{ws}",
                        "l2": "flushed (256 MB write) before every timed step"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                         "frac": achieved / peak,
+                         "traffic": profiled_traffic(f"slab{args.nx}x{args.ny}_{args.precision}_variant{variant}"),
+                         "peak_source": peak_kind,
                          "kernel": "collide" if cnt[0] > 0 else "fused_step", "variant": variant,
                          "kernel_ms": per_launch_ms, "step_kernels_ms": step_kernel_ms,
                          "algorithmic_bytes_per_launch": alg_bytes,
@@ -280,6 +350,8 @@ def run_ours(args, ws, rank, local):
             "wall_s": t_wall,
         }
         out.update(extra)
+        if ws == 1 and not args.no_forms:
+            out["forms"] = other_forms(stream, torch, lbm)
         if ws == 1 and not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(W.slab(nx=128, ny=128, steps=1, name="slab_128x128_sample"),
                                                seconds=args.cpu_seconds)
@@ -330,6 +402,7 @@ def main():
     ap.add_argument("--ny", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / adjoint / reactive form lines")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--variant", type=int, default=None, help="kernel form (-1 two-pass, >= 0 fused tile); default: autotune")
     args = ap.parse_args()

@@ -6,8 +6,8 @@
 // Newton's method (analytic sparse Jacobian, Gaussian elimination with
 // partial pivoting, steps shortened so that no concentration crosses zero).
 // Rates, residual and extents are FP64 whatever the population precision;
-// the Jacobian is FP64 on the FP64 path and FP32 on the FP32 path
-// (iterative refinement to the same FP64 root).  Then the gas mass production
+// the Jacobian is FP64 on the FP64 path and FP32 on the FP32 path, and is
+// reused across iterations (iterative refinement to the same FP64 root).  Then the gas mass production
 // (eq:totalFluidReactionRate, eq:molarToMassRates), the new coverages
 // (eq:surfaceMoleFractions, eq:totalSurfaceReactionRate without edges) and
 // the change of the fluid internal energy that keeps the unified internal
@@ -53,8 +53,11 @@ __device__ __forceinline__ double ipow(double x, int n) {
 //
 // Mixed precision (iterative refinement): concentrations, rates, the
 // residual F = xi - dt r(xi) and the extents are FP64; the Jacobian of F is
-// assembled and factorised in FP32 (RK = float) or FP64 (RK = double).  The
-// FP64 residual fixes the root, so both converge to the FP64 solution.
+// assembled and LU-factorised in FP32 (RK = float) or FP64 (RK = double)
+// and reused across iterations (simplified Newton) until the contraction of
+// the steps slows down or a step is shortened, when it is rebuilt at the
+// current iterate.  The FP64 residual fixes the root, so every variant
+// converges to the same FP64 solution.
 template <int M, class RK>
 __device__ void surface_source_dev(const MechDev& mc, double T, const double* rho_a, double phi, const double* Xs0,
                                    double* rhodot, double* Xs1, double& dU, int* status) {
@@ -67,9 +70,11 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
     xi[k] = 0.0;
   }
   const double scale = mc.a_s / phi;     // gas concentration change per extent
-  RK J[RMAX][RMAX + 1];
-  bool converged = false;
-  for (int it = 0; it < 30; ++it) {
+  RK LU[RMAX][RMAX];
+  int swp[RMAX];
+  bool refresh = true, converged = false;
+  double prev = 0.0;
+  for (int it = 0; it < 40; ++it) {
     double c[MMAX + SMAX], r[RMAX];
     for (int i = 0; i < NS; ++i) {
       double d = 0.0;
@@ -81,38 +86,55 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
       for (int j = 0; j < mc.nre[k]; ++j) v *= ipow(fmax(c[mc.ridx[k][j]], 0.0), mc.rord[k][j]);
       r[k] = v;
     }
-    // J = I - dt dr/dxi: only the reactants of step k enter row k
-    for (int k = 0; k < Rn; ++k) {
-      for (int l = 0; l < Rn; ++l) J[k][l] = (k == l) ? RK(1) : RK(0);
-      for (int j = 0; j < mc.nre[k]; ++j) {
-        const int i = mc.ridx[k][j];
-        if (c[i] > 0.0) {
-          const double g = mc.dt * r[k] * mc.rord[k][j] / c[i] * (i < M ? scale : 1.0);
-          for (int l = 0; l < Rn; ++l) J[k][l] -= RK(g * mc.nu_all[l][i]);
+    if (refresh) {
+      // J = I - dt dr/dxi: only the reactants of step k enter row k
+      for (int k = 0; k < Rn; ++k) {
+        for (int l = 0; l < Rn; ++l) LU[k][l] = (k == l) ? RK(1) : RK(0);
+        for (int j = 0; j < mc.nre[k]; ++j) {
+          const int i = mc.ridx[k][j];
+          if (c[i] > 0.0) {
+            const double g = mc.dt * r[k] * mc.rord[k][j] / c[i] * (i < M ? scale : 1.0);
+            for (int l = 0; l < Rn; ++l) LU[k][l] -= RK(g * mc.nu_all[l][i]);
+          }
         }
       }
-      J[k][Rn] = RK(-(xi[k] - mc.dt * r[k]));
-    }
-    for (int cc = 0; cc < Rn; ++cc) {
-      int pv = cc;
-      for (int k = cc + 1; k < Rn; ++k)
-        if (fabs(J[k][cc]) > fabs(J[pv][cc])) pv = k;
-      if (pv != cc)
-        for (int l = 0; l <= Rn; ++l) {
-          RK t = J[cc][l];
-          J[cc][l] = J[pv][l];
-          J[pv][l] = t;
+      // LU factors with partial pivoting (row swaps recorded in swp)
+      for (int cc = 0; cc < Rn; ++cc) {
+        int pv = cc;
+        for (int k = cc + 1; k < Rn; ++k)
+          if (fabs(LU[k][cc]) > fabs(LU[pv][cc])) pv = k;
+        swp[cc] = pv;
+        if (pv != cc)
+          for (int l = 0; l < Rn; ++l) {
+            RK t = LU[cc][l];
+            LU[cc][l] = LU[pv][l];
+            LU[pv][l] = t;
+          }
+        const RK inv = RK(1) / LU[cc][cc];
+        for (int k = cc + 1; k < Rn; ++k) {
+          const RK f = LU[k][cc] * inv;
+          LU[k][cc] = f;
+          for (int l = cc + 1; l < Rn; ++l) LU[k][l] -= f * LU[cc][l];
         }
-      for (int k = cc + 1; k < Rn; ++k) {
-        RK f = J[k][cc] / J[cc][cc];
-        for (int l = cc; l <= Rn; ++l) J[k][l] -= f * J[cc][l];
       }
+      refresh = false;
     }
+    // solve J dxi = -F with the stored factors
+    RK b[RMAX];
+    for (int k = 0; k < Rn; ++k) b[k] = RK(-(xi[k] - mc.dt * r[k]));
+    for (int cc = 0; cc < Rn; ++cc)
+      if (swp[cc] != cc) {
+        RK t = b[cc];
+        b[cc] = b[swp[cc]];
+        b[swp[cc]] = t;
+      }
+    for (int k = 1; k < Rn; ++k)
+      for (int l = 0; l < k; ++l) b[k] -= LU[k][l] * b[l];
     double dxi[RMAX];
     for (int k = Rn - 1; k >= 0; --k) {
-      RK s2 = J[k][Rn];
-      for (int l = k + 1; l < Rn; ++l) s2 -= J[k][l] * RK(dxi[l]);
-      dxi[k] = (double)(s2 / J[k][k]);
+      RK s2 = b[k];
+      for (int l = k + 1; l < Rn; ++l) s2 -= LU[k][l] * RK(dxi[l]);
+      dxi[k] = (double)(s2 / LU[k][k]);
     }
     // steps that would take a non-negative concentration below zero are shortened
     double alpha = 1.0;
@@ -132,6 +154,9 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
       converged = true;
       break;
     }
+    // rebuild the Jacobian when a step was shortened or the steps stop contracting fast
+    refresh = (alpha < 1.0) || (it > 0 && dmax > 0.25 * prev);
+    prev = dmax;
   }
   if (!converged) flag(status, 4);
   for (int a = 0; a < M; ++a) {

@@ -4,6 +4,7 @@
 #include "lbm_kernels.cuh"
 #include "lbm_march2d.cuh"
 #include "lbm_ops.h"
+#include "lbm_staged.cuh"
 #include "lbm_surface.cuh"
 
 namespace lbm {
@@ -63,6 +64,21 @@ struct Launch {
       }
     }
   }
+  // two-pass form whose node update stages each node's pulled populations in shared memory
+  template <int TB>
+  static int staged(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, cudaStream_t s) {
+    constexpr size_t smem = sizeof(R) * (size_t)n_pops<R, D, M, EN>() * TB;
+    if constexpr (smem > kMaxSmem) {
+      return -1;
+    } else {
+      auto kern = k_collide_staged<R, D, M, EN, TB>;
+      static bool done = false;
+      if (configure(kern, smem, done)) return -1;
+      k_macro<R, D, M, EN><<<grid(p.N), 256, 0, s>>>(p, it, a);
+      kern<<<(p.N + TB - 1) / TB, TB, smem, s>>>(p, it, a);
+      return 0;
+    }
+  }
   static int fused(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, int v, cudaStream_t s) {
     if constexpr (D == 2) {
       switch (v) {
@@ -72,6 +88,8 @@ struct Launch {
         case 3: return march2d<128, 4, 1, 1>(p, it, a, s);
         case 4: return march2d<64, 16, 1, 1>(p, it, a, s);
         case 5: return fused_tile<32, 1, 8>(p, it, a, s);
+        case 6: return staged<64>(p, it, a, s);
+        case 7: return staged<128>(p, it, a, s);
         default: return -1;
       }
     } else {
@@ -79,11 +97,13 @@ struct Launch {
         case 0: return fused_tile<32, 4, 16>(p, it, a, s);
         case 1: return fused_tile<32, 8, 16>(p, it, a, s);
         case 2: return fused_tile<32, 4, 8>(p, it, a, s);
+        case 3: return staged<64>(p, it, a, s);
+        case 4: return staged<32>(p, it, a, s);
         default: return -1;
       }
     }
   }
-  static constexpr int n_variants = (D == 2) ? 6 : 3;
+  static constexpr int n_variants = (D == 2) ? 8 : 5;
   static void init(const Params<R>& p, const double* X, const double* T, const double* P, const double* U,
                    double cvel, double RU, R* dst, const R* phi, cudaStream_t s) {
     k_init<R, D, M, EN><<<grid(p.N), 256, 0, s>>>(p, X, T, P, U, cvel, RU, dst, phi);
@@ -99,7 +119,18 @@ struct Launch {
   }
   static void react_collide(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, const ReactArgs& ra,
                             cudaStream_t s) {
-    if constexpr (has_react) k_collide_react<R, D, M, EN><<<(p.N + 127) / 128, 128, 0, s>>>(p, it, a, ra);
+    if constexpr (has_react) {
+      // node populations staged in shared memory (TB x 216 values per block)
+      constexpr int TB = sizeof(R) == 4 ? 64 : 32;
+      constexpr size_t smem = sizeof(R) * (size_t)n_pops<R, D, M, EN>() * TB;
+      auto kern = k_collide_react_staged<R, D, M, EN, TB>;
+      static bool done = false;
+      if (configure(kern, smem, done)) {
+        k_collide_react<R, D, M, EN><<<(p.N + 127) / 128, 128, 0, s>>>(p, it, a, ra);
+        return;
+      }
+      kern<<<(p.N + TB - 1) / TB, TB, smem, s>>>(p, it, a, ra);
+    }
   }
   static Ops<R> ops() {
     return Ops<R>{macro, collide, fused, n_variants, init, moments, has_react ? react_macro : nullptr,

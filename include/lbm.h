@@ -110,7 +110,9 @@ typedef struct lbm_config {
   const double* X_in_hi;       /* [M] reservoir composition at x = nx-1 */
   double T_in_lo, T_in_hi, P_in_lo, P_in_hi;
   /* surface mechanism (Sec. 4): S == 0 for none */
-  int S, R;                    /* surface species (<= 12), reactions (<= 32) */
+  int S, R;                    /* surface species (<= 12), reactions (<= 32); every step has
+                                  integer reactant orders, at most 4 reactants and at most 8
+                                  species with nonzero stoichiometry (else LBM_ERR_ARG) */
   const double* nu_gas;        /* [R*M] signed stoichiometry, gas */
   const double* nu_surf;       /* [R*S] signed stoichiometry, surface */
   const double* A_pre;         /* [R] Arrhenius prefactors (SI for the order) */

@@ -193,6 +193,12 @@ static int setup_surface(lbm_ctx* x, const lbm_config* c) {
       if (a < c->M) h.nu_g[k][a] = v;
       else h.nu_s[k][a - c->M] = v;
       h.nu_all[k][a] = v;
+      if (v != 0) {
+        if (h.npart[k] >= 8) return fail(nullptr, LBM_ERR_ARG, "at most 8 species take part in one surface step");
+        h.pidx[k][h.npart[k]] = a;
+        h.pnu[k][h.npart[k]] = v;
+        h.npart[k]++;
+      }
       if (v < 0) {
         // mass-action reactant with an integer order
         const double ord = -v;

@@ -72,9 +72,10 @@ struct Launch {
       return -1;
     } else {
       auto kern = k_collide_staged<R, D, M, EN, TB>;
-      static bool done = false;
-      if (configure(kern, smem, done)) return -1;
-      k_macro<R, D, M, EN><<<grid(p.N), 256, 0, s>>>(p, it, a);
+      auto kmac = k_macro_staged<R, D, M, EN, TB>;
+      static bool done = false, done_mac = false;
+      if (configure(kern, smem, done) || configure(kmac, smem, done_mac)) return -1;
+      kmac<<<(p.N + TB - 1) / TB, TB, smem, s>>>(p, it, a);
       kern<<<(p.N + TB - 1) / TB, TB, smem, s>>>(p, it, a);
       return 0;
     }

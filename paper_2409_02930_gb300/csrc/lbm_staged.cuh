@@ -55,6 +55,38 @@ __device__ __forceinline__ void staged_state(const Params<R>& p, const StepArgs<
   gr.compute(p, x, y, z, [&](int k, int nb) { return mac[(size_t)k * N + nb]; });
 }
 
+// Macro-field pass (u, Pi_alpha, Y_a for the neighbours' gradients) from staged populations.
+template <class R, int D, int M, bool EN, int TB>
+__global__ void __launch_bounds__(TB) k_macro_staged(Params<R> p, InletTables<R> it, StepArgs<R> a) {
+  extern __shared__ unsigned char smem_raw[];
+  R* col = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
+  const int n = blockIdx.x * TB + threadIdx.x;
+  if (n >= p.N) return;
+  int x, y, z;
+  node_xyz<R, D>(p, n, x, y, z);
+  Site<R, D> st;
+  st.init(p, x, y, z);
+  Ghost<R, D> gh;
+  gh.side = -1;
+  if (st.has_ghost()) ghost_velocity<R, D, M>(p, a.src, a.phi, x, y, z, gh);
+  stage_node<R, D, M, EN>(p, it, a.src, st, gh, col, TB);
+  SmemPull<R, D> pf{col, TB};
+  Moments<R, D, M, EN, false> mo;
+  moments_gen<R, D, M, EN, false>(pf, mo);
+  State<R, D, M> s;
+  s.template from_moments<EN, false>(p, mo, a.phi[n], EN ? R(0) : a.Tfix[n]);
+  const size_t N = p.N;
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    a.mac[(size_t)b * N + n] = s.u[b];
+    a.mac[(size_t)(D + b) * N + n] = s.Pi(b);
+  }
+  if (EN) {
+#pragma unroll
+    for (int k = 0; k < M; ++k) a.mac[(size_t)(2 * D + k) * N + n] = s.Y[k];
+  }
+}
+
 template <class R, int D, int M, bool EN, int TB>
 __global__ void __launch_bounds__(TB) k_collide_staged(Params<R> p, InletTables<R> it, StepArgs<R> a) {
   extern __shared__ unsigned char smem_raw[];

@@ -29,6 +29,9 @@ struct MechDev {
   double nu_g[RMAX][MMAX];
   double nu_s[RMAX][SMAX];
   double nu_all[RMAX][MMAX + SMAX];
+  int npart[RMAX];                   // species taking part in each step (nonzero stoichiometry)
+  int pidx[RMAX][8];
+  double pnu[RMAX][8];
   int nre[RMAX];                     // reactants of each step
   int ridx[RMAX][4];
   int rord[RMAX][4];
@@ -76,11 +79,12 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
   double prev = 0.0;
   for (int it = 0; it < 40; ++it) {
     double c[MMAX + SMAX], r[RMAX];
-    for (int i = 0; i < NS; ++i) {
-      double d = 0.0;
-      for (int k = 0; k < Rn; ++k) d += mc.nu_all[k][i] * xi[k];
-      c[i] = c0[i] + (i < M ? scale : 1.0) * d;
-    }
+    // c = c0 + (scaled) nu^T xi, over the few species of each step
+    double d[MMAX + SMAX];
+    for (int i = 0; i < NS; ++i) d[i] = 0.0;
+    for (int k = 0; k < Rn; ++k)
+      for (int j = 0; j < mc.npart[k]; ++j) d[mc.pidx[k][j]] += mc.pnu[k][j] * xi[k];
+    for (int i = 0; i < NS; ++i) c[i] = c0[i] + (i < M ? scale : 1.0) * d[i];
     for (int k = 0; k < Rn; ++k) {
       double v = kr[k];
       for (int j = 0; j < mc.nre[k]; ++j) v *= ipow(fmax(c[mc.ridx[k][j]], 0.0), mc.rord[k][j]);
@@ -138,11 +142,15 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
     }
     // steps that would take a non-negative concentration below zero are shortened
     double alpha = 1.0;
-    for (int i = 0; i < NS; ++i) {
-      double d = 0.0;
-      for (int k = 0; k < Rn; ++k) d += mc.nu_all[k][i] * dxi[k];
-      d *= (i < M ? scale : 1.0);
-      if (c[i] >= 0.0 && c[i] + d < 0.0) alpha = fmin(alpha, 0.9 * c[i] / (-d));
+    {
+      double dd[MMAX + SMAX];
+      for (int i = 0; i < NS; ++i) dd[i] = 0.0;
+      for (int k = 0; k < Rn; ++k)
+        for (int j = 0; j < mc.npart[k]; ++j) dd[mc.pidx[k][j]] += mc.pnu[k][j] * dxi[k];
+      for (int i = 0; i < NS; ++i) {
+        const double di = dd[i] * (i < M ? scale : 1.0);
+        if (c[i] >= 0.0 && c[i] + di < 0.0) alpha = fmin(alpha, 0.9 * c[i] / (-di));
+      }
     }
     double dmax = 0.0, xmax = 0.0;
     for (int k = 0; k < Rn; ++k) {

@@ -198,6 +198,10 @@ static int setup_surface(lbm_ctx* x, const lbm_config* c) {
         h.pidx[k][h.npart[k]] = a;
         h.pnu[k][h.npart[k]] = v;
         h.npart[k]++;
+        h.sr_k[a][h.nsr[a]] = k;
+        h.sr_nuf[a][h.nsr[a]] = (float)v;
+        h.sr_nud[a][h.nsr[a]] = v;
+        h.nsr[a]++;
       }
       if (v < 0) {
         // mass-action reactant with an integer order

@@ -32,6 +32,10 @@ struct MechDev {
   int npart[RMAX];                   // species taking part in each step (nonzero stoichiometry)
   int pidx[RMAX][8];
   double pnu[RMAX][8];
+  int nsr[MMAX + SMAX];               // steps in which each species takes part
+  int sr_k[MMAX + SMAX][RMAX];
+  float sr_nuf[MMAX + SMAX][RMAX];
+  double sr_nud[MMAX + SMAX][RMAX];
   int nre[RMAX];                     // reactants of each step
   int ridx[RMAX][4];
   int rord[RMAX][4];
@@ -43,6 +47,11 @@ struct MechDev {
   double dt;                         // physical time step [s]
   double cvel2;                      // (dx/dt)^2 [m^2/s^2]
 };
+
+// stoichiometric coefficient of species i in its q-th step, in the Jacobian's precision
+template <class RK> __device__ __forceinline__ RK sr_nu(const MechDev& mc, int i, int q);
+template <> __device__ __forceinline__ float sr_nu<float>(const MechDev& mc, int i, int q) { return mc.sr_nuf[i][q]; }
+template <> __device__ __forceinline__ double sr_nu<double>(const MechDev& mc, int i, int q) { return mc.sr_nud[i][q]; }
 
 __device__ __forceinline__ double ipow(double x, int n) {
   double r = 1.0;
@@ -97,8 +106,9 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
         for (int j = 0; j < mc.nre[k]; ++j) {
           const int i = mc.ridx[k][j];
           if (c[i] > 0.0) {
-            const double g = mc.dt * r[k] * mc.rord[k][j] / c[i] * (i < M ? scale : 1.0);
-            for (int l = 0; l < Rn; ++l) LU[k][l] -= RK(g * mc.nu_all[l][i]);
+            // d r_k / d xi_l = r_k ord / c_i dc_i/dxi_l: only the steps l in which species i takes part
+            const RK g = RK(mc.dt * r[k] * mc.rord[k][j] / c[i] * (i < M ? scale : 1.0));
+            for (int q = 0; q < mc.nsr[i]; ++q) LU[k][mc.sr_k[i][q]] -= g * sr_nu<RK>(mc, i, q);
           }
         }
       }
@@ -167,15 +177,15 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
     prev = dmax;
   }
   if (!converged) flag(status, 4);
-  for (int a = 0; a < M; ++a) {
-    double dn = 0.0;
-    for (int k = 0; k < Rn; ++k) dn += mc.nu_g[k][a] * xi[k];
-    rhodot[a] = mc.a_s * mc.m[a] * dn;
-  }
+  // moles produced per unit surface, nu^T xi, over the few species of each step
+  double dn_all[MMAX + SMAX];
+  for (int i = 0; i < NS; ++i) dn_all[i] = 0.0;
+  for (int k = 0; k < Rn; ++k)
+    for (int j = 0; j < mc.npart[k]; ++j) dn_all[mc.pidx[k][j]] += mc.pnu[k][j] * xi[k];
+  for (int a = 0; a < M; ++a) rhodot[a] = mc.a_s * mc.m[a] * dn_all[a];
   double dUs = 0.0;
   for (int s = 0; s < S; ++s) {
-    double dn = 0.0;
-    for (int k = 0; k < Rn; ++k) dn += mc.nu_s[k][s] * xi[k];
+    const double dn = dn_all[M + s];
     Xs1[s] = Xs0[s] + dn / mc.gamma;
     const double Us = mc.Us0[s] + mc.cvs[s] * R_UNIV_DEV * (T - mc.T_thermo);
     dUs += mc.a_s * dn * Us;

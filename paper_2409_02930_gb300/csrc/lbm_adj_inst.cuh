@@ -5,7 +5,8 @@
 namespace lbm {
 namespace {
 
-constexpr int kLanes = 8;
+constexpr int kLanes = 4;        // dual lanes of the node-update evaluations
+constexpr int kLanesSmall = 8;   // dual lanes of the macro-field and reservoir-ghost evaluations
 
 template <class To, class From>
 void params_cast(const Params<From>& s, Params<To>& d) {
@@ -26,9 +27,10 @@ void params_cast(const Params<From>& s, Params<To>& d) {
 
 template <class B, int D, int M, bool EN>
 struct AdjLaunch {
-  static constexpr int K = kLanes;
-  static AdjParams<B, K> make(const Params<B>& p) {
-    AdjParams<B, K> ap;
+  static constexpr int K = kLanes, KS = kLanesSmall;
+  template <int KK>
+  static AdjParams<B, KK> make(const Params<B>& p) {
+    AdjParams<B, KK> ap;
     params_cast(p, ap.pz);
     ap.pz.N = 1;                 // node-local evaluation into a local array
     ap.pk = ap.pz;
@@ -37,15 +39,15 @@ struct AdjLaunch {
   }
   static int grid(int n, int b) { return (n + b - 1) / b; }
   static int collide(const Params<B>& p, const InletTables<B>& it, const AdjArgs<B>& a, cudaStream_t s) {
-    k_adj_collide<B, D, M, EN, K><<<grid(p.N, 128), 128, 0, s>>>(p, it, a, make(p));
+    k_adj_collide<B, D, M, EN, K><<<grid(p.N, 128), 128, 0, s>>>(p, it, a, make<K>(p));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
   }
   static int macro(const Params<B>& p, const InletTables<B>& it, const AdjArgs<B>& a, cudaStream_t s) {
-    k_adj_macro<B, D, M, EN, K><<<grid(p.N, 128), 128, 0, s>>>(p, it, a, make(p));
+    k_adj_macro<B, D, M, EN, KS><<<grid(p.N, 128), 128, 0, s>>>(p, it, a, make<KS>(p));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
   }
   static int ghost(const Params<B>& p, const InletTables<B>& it, const AdjArgs<B>& a, cudaStream_t s) {
-    k_adj_ghost<B, D, M, EN, K><<<grid(p.ny * p.nz, 128), 128, 0, s>>>(p, it, a, make(p));
+    k_adj_ghost<B, D, M, EN, KS><<<grid(p.ny * p.nz, 128), 128, 0, s>>>(p, it, a, make<KS>(p));
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
   }
   static void stream(const Params<B>& p, const AdjArgs<B>& a, cudaStream_t s) {

@@ -51,13 +51,22 @@ struct AdjArgs {
   int* status;
 };
 
-// Streamed populations held in a local array (the node's inputs).
-template <class T, int D, int M, bool EN>
-struct LocalPull {
-  const T* P;
+// Streamed populations of the node (base type), returned as dual numbers:
+// population j carries derivative 1 in lane j - first when that lane lies
+// in [0, K) (the directions of the current evaluation).
+template <class B, int K, int D, int M, bool EN>
+struct SeededPull {
+  const B* P;
+  int first;
   static constexpr bool kUnroll = false;
   LBM_HD int prep(int, int, int) const { return 0; }
-  LBM_HD T get(int, int l, int i, int, int, int) const { return P[l * Lat<D>::Q + i]; }
+  LBM_HD Dual<B, K> get(int, int l, int i, int, int, int) const {
+    const int j = l * Lat<D>::Q + i;
+    Dual<B, K> v(P[j]);
+    const int lane = j - first;
+    if (lane >= 0 && lane < K) v.d[lane] = B(1);
+    return v;
+  }
 };
 
 // Streamed populations of node n (base type) with the boundary rules.
@@ -102,13 +111,6 @@ __global__ void __launch_bounds__(128) k_adj_collide(Params<B> p, InletTables<B>
   double pb_phi = 0.0, pb_k = 0.0;
 #pragma unroll 1
   for (int c0 = 0; c0 < ND; c0 += K) {
-    T Pd[LQ];
-#pragma unroll
-    for (int j = 0; j < LQ; ++j) {
-      Pd[j] = T(P[j]);
-      const int dir = 2 + NG + j - c0;
-      if (dir >= 0 && dir < K) Pd[j].d[dir] = B(1);
-    }
     T phid(phin);
     if (1 - c0 >= 0 && 1 - c0 < K) phid.d[1 - c0] = B(1);
     Grad<T, D, M, EN> gd;
@@ -128,13 +130,13 @@ __global__ void __launch_bounds__(128) k_adj_collide(Params<B> p, InletTables<B>
         else gd.dY[k][b] = T(B(0));
       }
     const Params<T>& pp = (c0 == 0) ? ap.pk : ap.pz;      // lambda is direction 0
-    LocalPull<T, D, M, EN> pf{Pd};
+    SeededPull<B, K, D, M, EN> pf{P, c0 - 2 - NG};
     Moments<T, D, M, EN, true> mo;
     moments_gen<T, D, M, EN, true>(pf, mo);
     State<T, D, M> s;
     s.template from_moments<EN, true>(pp, mo, phid, T(Tf));
     T out[LQ];
-    collide_gen<T, D, M, EN, LocalPull<T, D, M, EN>, false>(pp, pf, 0, mo, s, gd, out, a.status);
+    collide_gen<T, D, M, EN, SeededPull<B, K, D, M, EN>, false>(pp, pf, 0, mo, s, gd, out, a.status);
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int dir = c0 + k;

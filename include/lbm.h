@@ -145,10 +145,11 @@ int lbm_create(lbm_ctx** out, const lbm_config* cfg);
  * (3, on); the stream of cfgs[0] is used.  The cases are stepped together:
  * each lbm_step launches two persistent kernels (macro-field pass, node
  * update) over one work list of node tiles of all cases, replayed from a
- * CUDA graph of 50 steps.  Variants 0..5 select the tile length (64, 128,
- * 256 nodes for v/2 = 0, 1, 2) and the grid (v even: one block per resident
- * slot of every SM, looping over a contiguous range of tiles; v odd: one
- * block per tile); lbm_autotune picks among them.  Per-node outputs
+ * CUDA graph of 50 steps.  Variants 0..11 select the tile length (64, 128,
+ * 256 nodes for (v % 6)/2 = 0, 1, 2), the grid (v even: one block per
+ * resident slot of every SM, looping over a contiguous range of tiles; v odd:
+ * one block per tile) and, for v >= 6, the staging of every node's pulled
+ * populations in shared memory; lbm_autotune picks among them.  Per-node outputs
  * (lbm_moments, populations) are the concatenation over cases, in case
  * order, of each case's single-lattice layout.  Errors as lbm_create, plus
  * LBM_ERR_ARG for n_cases < 1 or cases of different kinds.

@@ -11,6 +11,7 @@
 #pragma once
 
 #include "lbm_kernels.cuh"
+#include "lbm_staged.cuh"
 
 namespace lbm {
 
@@ -51,6 +52,27 @@ __global__ void __launch_bounds__(TB) k_batch(BatchArgs<R> b) {
                   b.mac + cs.mac_off, b.status};
     if (COLLIDE) collide_node<R, D, M, EN>(cs.p, cs.it, a, n);
     else macro_node<R, D, M, EN>(cs.p, cs.it, a, n);
+  }
+}
+
+// The same passes with every node's pulled populations staged in shared
+// memory (TB x L*Q values per block; a thread reuses its column for each of
+// its tiles).
+template <class R, int D, int M, bool EN, int TB, bool COLLIDE>
+__global__ void __launch_bounds__(TB) k_batch_staged(BatchArgs<R> b) {
+  extern __shared__ unsigned char smem_raw[];
+  R* col = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
+  const int t0 = (int)((long long)blockIdx.x * b.ntiles / gridDim.x);
+  const int t1 = (int)((long long)(blockIdx.x + 1) * b.ntiles / gridDim.x);
+  for (int t = t0; t < t1; ++t) {
+    const int2 tl = b.tiles[t];
+    const CaseDev<R>& cs = b.cases[tl.x];
+    const int n = tl.y + (int)threadIdx.x;
+    if (n >= cs.p.N) continue;
+    StepArgs<R> a{b.src + cs.pop_off, b.dst + cs.pop_off, b.phi + cs.node_off, b.Tfix + cs.node_off,
+                  b.mac + cs.mac_off, b.status};
+    if (COLLIDE) collide_staged_node<R, D, M, EN>(cs.p, cs.it, a, n, col, TB);
+    else macro_staged_node<R, D, M, EN>(cs.p, cs.it, a, n, col, TB);
   }
 }
 

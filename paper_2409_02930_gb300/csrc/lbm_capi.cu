@@ -583,7 +583,7 @@ constexpr int kGraphSteps = 50;    // even: a replay returns to the same ping-po
 
 template <class R>
 static lbm::BatchArgs<R> batch_args(lbm_ctx* x, int cur) {
-  const int t = x->variant / 2;
+  const int t = (x->variant % 6) / 2;
   return lbm::BatchArgs<R>{(const lbm::CaseDev<R>*)x->cases_dev, x->tiles_dev[t], x->ntiles[t],
                            (const R*)x->pops[cur], (R*)x->pops[1 - cur], (const R*)x->phi, (const R*)x->Tfix,
                            (R*)x->mac, x->status};
@@ -591,7 +591,7 @@ static lbm::BatchArgs<R> batch_args(lbm_ctx* x, int cur) {
 
 template <class R>
 static int batch_grid(lbm_ctx* x, const lbm::BatchOps<R>& ops) {
-  const int nt = x->ntiles[x->variant / 2];
+  const int nt = x->ntiles[(x->variant % 6) / 2];
   if (x->variant % 2) return nt;
   const int g = x->sm_count * ops.occupancy(x->variant);
   return g < nt ? g : nt;

@@ -55,13 +55,11 @@ __device__ __forceinline__ void staged_state(const Params<R>& p, const StepArgs<
   gr.compute(p, x, y, z, [&](int k, int nb) { return mac[(size_t)k * N + nb]; });
 }
 
-// Macro-field pass (u, Pi_alpha, Y_a for the neighbours' gradients) from staged populations.
-template <class R, int D, int M, bool EN, int TB>
-__global__ void __launch_bounds__(TB) k_macro_staged(Params<R> p, InletTables<R> it, StepArgs<R> a) {
-  extern __shared__ unsigned char smem_raw[];
-  R* col = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
-  const int n = blockIdx.x * TB + threadIdx.x;
-  if (n >= p.N) return;
+// Macro fields of node n (u, Pi_alpha, Y_a for the neighbours' gradients)
+// from its populations staged in col[(l*Q + i) * stride].
+template <class R, int D, int M, bool EN>
+__device__ __forceinline__ void macro_staged_node(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a,
+                                                  int n, R* col, int stride) {
   int x, y, z;
   node_xyz<R, D>(p, n, x, y, z);
   Site<R, D> st;
@@ -69,8 +67,8 @@ __global__ void __launch_bounds__(TB) k_macro_staged(Params<R> p, InletTables<R>
   Ghost<R, D> gh;
   gh.side = -1;
   if (st.has_ghost()) ghost_velocity<R, D, M>(p, a.src, a.phi, x, y, z, gh);
-  stage_node<R, D, M, EN>(p, it, a.src, st, gh, col, TB);
-  SmemPull<R, D> pf{col, TB};
+  stage_node<R, D, M, EN>(p, it, a.src, st, gh, col, stride);
+  SmemPull<R, D> pf{col, stride};
   Moments<R, D, M, EN, false> mo;
   moments_gen<R, D, M, EN, false>(pf, mo);
   State<R, D, M> s;
@@ -87,12 +85,10 @@ __global__ void __launch_bounds__(TB) k_macro_staged(Params<R> p, InletTables<R>
   }
 }
 
-template <class R, int D, int M, bool EN, int TB>
-__global__ void __launch_bounds__(TB) k_collide_staged(Params<R> p, InletTables<R> it, StepArgs<R> a) {
-  extern __shared__ unsigned char smem_raw[];
-  R* col = reinterpret_cast<R*>(smem_raw) + threadIdx.x;
-  const int n = blockIdx.x * TB + threadIdx.x;
-  if (n >= p.N) return;
+// Node update of node n from its staged populations.
+template <class R, int D, int M, bool EN>
+__device__ __forceinline__ void collide_staged_node(const Params<R>& p, const InletTables<R>& it,
+                                                    const StepArgs<R>& a, int n, R* col, int stride) {
   int x, y, z;
   node_xyz<R, D>(p, n, x, y, z);
   Site<R, D> st;
@@ -100,13 +96,30 @@ __global__ void __launch_bounds__(TB) k_collide_staged(Params<R> p, InletTables<
   Ghost<R, D> gh;
   gh.side = -1;
   if (st.has_ghost()) ghost_velocity<R, D, M>(p, a.src, a.phi, x, y, z, gh);
-  stage_node<R, D, M, EN>(p, it, a.src, st, gh, col, TB);
-  SmemPull<R, D> pf{col, TB};
+  stage_node<R, D, M, EN>(p, it, a.src, st, gh, col, stride);
+  SmemPull<R, D> pf{col, stride};
   Moments<R, D, M, EN, true> mo;
   State<R, D, M> s;
   Grad<R, D, M, EN> gr;
   staged_state<R, D, M, EN>(p, a, pf, n, x, y, z, mo, s, gr);
   collide_gen<R, D, M, EN>(p, pf, n, mo, s, gr, a.dst, a.status);
+}
+
+// Macro-field pass from staged populations.
+template <class R, int D, int M, bool EN, int TB>
+__global__ void __launch_bounds__(TB) k_macro_staged(Params<R> p, InletTables<R> it, StepArgs<R> a) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = blockIdx.x * TB + threadIdx.x;
+  if (n >= p.N) return;
+  macro_staged_node<R, D, M, EN>(p, it, a, n, reinterpret_cast<R*>(smem_raw) + threadIdx.x, TB);
+}
+
+template <class R, int D, int M, bool EN, int TB>
+__global__ void __launch_bounds__(TB) k_collide_staged(Params<R> p, InletTables<R> it, StepArgs<R> a) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = blockIdx.x * TB + threadIdx.x;
+  if (n >= p.N) return;
+  collide_staged_node<R, D, M, EN>(p, it, a, n, reinterpret_cast<R*>(smem_raw) + threadIdx.x, TB);
 }
 
 // Reactive node update (surface sources of the first pass) from staged populations.

@@ -54,7 +54,7 @@ def test_every_batch_variant_and_graph_path_agree(L):
     b0 = L.Batch(wls, precision=L.LBM_FP64)
     nv = b0.variant_count()
     b0.close()
-    assert nv == 6
+    assert nv == 12
     for v in range(nv):
         b = L.Batch(wls, precision=L.LBM_FP64)
         b.set_variant(v)
@@ -83,7 +83,7 @@ def test_fp32_batch_full_size_matches_single_cases(L):
     b = L.Batch(wls, precision=L.LBM_FP32)
     assert b.N == sum(w.N for w in wls)
     best = b.autotune(3)
-    assert 0 <= best < 6
+    assert 0 <= best < 12
     b.close()
     b = L.Batch(wls, precision=L.LBM_FP32)
     b.set_variant(best)

@@ -55,9 +55,11 @@ struct Launch {
       if constexpr (smem > kMaxSmem) {
         return -1;
       } else {
-        auto kern = k_march2d<R, M, EN, TX, SEG, MINB, PD>;
-        static bool done = false;
-        if (configure(kern, smem, done)) return -1;
+        // the reservoir-column path is compiled in only when a face is a reservoir
+        const bool inlet = p.bc_lo == BC_INLET || p.bc_hi == BC_INLET;
+        auto kern = inlet ? k_march2d<R, M, EN, TX, SEG, MINB, PD, true> : k_march2d<R, M, EN, TX, SEG, MINB, PD, false>;
+        static bool done[2] = {false, false};
+        if (configure(kern, smem, done[inlet ? 1 : 0])) return -1;
         dim3 g((p.nx + TX - 3) / (TX - 2), (p.ny + SEG - 1) / SEG, 1);
         kern<<<g, TX, smem, s>>>(p, it, a);
         return 0;

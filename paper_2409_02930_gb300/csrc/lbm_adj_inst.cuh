@@ -5,10 +5,11 @@
 namespace lbm {
 namespace {
 
-// dual lanes of the node-update evaluations: fewer lanes spill less (FP32,
-// 2 lanes: 1.65 ms per adjoint step of the 256x256 slab, 4 lanes: 2.87 ms),
-// more lanes repeat the value part less often (FP64, ALU bound: 4 lanes)
-template <class B> constexpr int kLanesOf() { return sizeof(B) == 4 ? 2 : 4; }
+// dual lanes of the node-update evaluations: fewer lanes spill less (with
+// populations seeded, FP32 took 1.65 ms per adjoint step of the 256x256 slab
+// with 2 lanes and 2.87 ms with 4); with the moments seeded, 4 lanes in FP64
+// push the node code past the register file into a 13 KB stack frame
+template <class B> constexpr int kLanesOf() { return 2; }
 constexpr int kLanesSmall = 8;   // dual lanes of the macro-field and reservoir-ghost evaluations
 
 template <class To, class From>

@@ -51,24 +51,6 @@ struct AdjArgs {
   int* status;
 };
 
-// Streamed populations of the node (base type), returned as dual numbers:
-// population j carries derivative 1 in lane j - first when that lane lies
-// in [0, K) (the directions of the current evaluation).
-template <class B, int K, int D, int M, bool EN>
-struct SeededPull {
-  const B* P;
-  int first;
-  static constexpr bool kUnroll = false;
-  LBM_HD int prep(int, int, int) const { return 0; }
-  LBM_HD Dual<B, K> get(int, int l, int i, int, int, int) const {
-    const int j = l * Lat<D>::Q + i;
-    Dual<B, K> v(P[j]);
-    const int lane = j - first;
-    if (lane >= 0 && lane < K) v.d[lane] = B(1);
-    return v;
-  }
-};
-
 // Streamed populations of node n (base type) with the boundary rules.
 template <class B, int D, int M, bool EN>
 LBM_HD void pull_node(const Params<B>& p, const InletTables<B>& it, const B* f, const B* phi, int x, int y, int z,
@@ -86,13 +68,76 @@ LBM_HD void pull_node(const Params<B>& p, const InletTables<B>& it, const B* f, 
   });
 }
 
-// Node update: lambda^{n+1}(x)^T dC / d(lambda, phi(x), G(x), P(x)).
+// Streamed populations of the node as dual numbers with zero derivative: the
+// node update's dependence on them is split into the moments (seeded) and
+// the direct relaxation term (coefficient returned by collide_gen).
+template <class B, int K, int D, int M, bool EN>
+struct PlainPull {
+  const B* P;
+  static constexpr bool kUnroll = false;
+  LBM_HD int prep(int, int, int) const { return 0; }
+  LBM_HD Dual<B, K> get(int, int l, int i, int, int, int) const { return Dual<B, K>(P[l * Lat<D>::Q + i]); }
+};
+
+// Moments seeded in the dual lanes [first, first + K) of a running index
+// (sa, ja, sf, jf, Pt, sg, q in that order).
+template <class B, int K, int D, int M, bool EN>
+LBM_HD void seed_moments(const Moments<B, D, M, EN, true>& m0, int first, Moments<Dual<B, K>, D, M, EN, true>& mo) {
+  using T = Dual<B, K>;
+  int idx = 0;
+  auto put = [&](T& dst, B v) {
+    dst = T(v);
+    const int lane = idx - first;
+    if (lane >= 0 && lane < K) dst.d[lane] = B(1);
+    ++idx;
+  };
+#pragma unroll
+  for (int a = 0; a < M; ++a) put(mo.sa[a], m0.sa[a]);
+#pragma unroll
+  for (int a = 0; a < M; ++a)
+#pragma unroll
+    for (int b = 0; b < D; ++b) put(mo.ja[a][b], m0.ja[a][b]);
+  put(mo.sf, m0.sf);
+#pragma unroll
+  for (int b = 0; b < D; ++b) put(mo.jf[b], m0.jf[b]);
+#pragma unroll
+  for (int b = 0; b < D; ++b)
+#pragma unroll
+    for (int c = 0; c < D; ++c) put(mo.Pt[b][c], m0.Pt[b][c]);
+  put(mo.sg, m0.sg);
+#pragma unroll
+  for (int b = 0; b < D; ++b) put(mo.q[b], m0.q[b]);
+#pragma unroll
+  for (int a = 0; a < M; ++a) mo.sabs[a] = T(m0.sabs[a]);     // a resolution test only: no derivative
+}
+
+template <int D, int M>
+LBM_HD constexpr int n_mom() { return M + M * D + 1 + D + D * D + 1 + D; }
+
+// Base-type puller over the node's streamed populations.
+template <class B, int D>
+struct BasePull {
+  const B* P;
+  static constexpr bool kUnroll = false;
+  LBM_HD int prep(int, int, int) const { return 0; }
+  LBM_HD B get(int, int l, int i, int, int, int) const { return P[l * Lat<D>::Q + i]; }
+};
+
+// Node update: lambda^{n+1}(x)^T dC / d(lambda, phi(x), G(x), P(x)).  The
+// populations enter the node update through the moments and through the
+// direct relaxation term: dC_{l,i}/dP_{l,j} = coef_l delta_ij for i, j not
+// the rest velocity, and the rest population (a conservation remainder)
+// carries -coef_l.  Dual evaluations seed lambda, phi, the gradient inputs
+// and the moments; the populations' adjoint follows from the moments'
+// transpose plus the direct term.
 template <class B, int D, int M, bool EN, int K>
 __global__ void __launch_bounds__(128) k_adj_collide(Params<B> p, InletTables<B> it, AdjArgs<B> a,
                                                      const __grid_constant__ AdjParams<B, K> ap) {
   using T = Dual<B, K>;
   constexpr int Q = Lat<D>::Q, L = n_lat<D, M, EN>(), LQ = L * Q, NG = n_grad<D, M, EN>();
-  constexpr int ND = 2 + NG + LQ;     // directions: lambda, phi, gradients, populations
+  constexpr int NM = n_mom<D, M>();
+  constexpr int ND = 2 + NG + NM;     // directions: lambda, phi, gradients, moments
+  constexpr int REST = (Q - 1) / 2;
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= p.N) return;
   const int N = p.N;
@@ -100,6 +145,8 @@ __global__ void __launch_bounds__(128) k_adj_collide(Params<B> p, InletTables<B>
   node_xyz<B, D>(p, n, x, y, z);
   B P[LQ];
   pull_node<B, D, M, EN>(p, it, a.f, a.phi, x, y, z, P);
+  Moments<B, D, M, EN, true> m0;
+  moments_gen<B, D, M, EN, true>(BasePull<B, D>{P}, m0);
   Grad<B, D, M, EN> g0;
   const B* __restrict__ mac = a.mac;
   g0.compute(p, x, y, z, [&](int k, int nb) { return mac[(size_t)k * N + nb]; });
@@ -109,6 +156,7 @@ __global__ void __launch_bounds__(128) k_adj_collide(Params<B> p, InletTables<B>
 #pragma unroll
   for (int j = 0; j < LQ; ++j) lam[j] = a.lam1[(size_t)j * N + n];
   double pb_phi = 0.0, pb_k = 0.0;
+  B mbar[NM], coef[L];
 #pragma unroll 1
   for (int c0 = 0; c0 < ND; c0 += K) {
     T phid(phin);
@@ -130,13 +178,15 @@ __global__ void __launch_bounds__(128) k_adj_collide(Params<B> p, InletTables<B>
         else gd.dY[k][b] = T(B(0));
       }
     const Params<T>& pp = (c0 == 0) ? ap.pk : ap.pz;      // lambda is direction 0
-    SeededPull<B, K, D, M, EN> pf{P, c0 - 2 - NG};
     Moments<T, D, M, EN, true> mo;
-    moments_gen<T, D, M, EN, true>(pf, mo);
+    seed_moments<B, K, D, M, EN>(m0, c0 - 2 - NG, mo);
+    PlainPull<B, K, D, M, EN> pf{P};
     State<T, D, M> s;
     s.template from_moments<EN, true>(pp, mo, phid, T(Tf));
-    T out[LQ];
-    collide_gen<T, D, M, EN, SeededPull<B, K, D, M, EN>, false>(pp, pf, 0, mo, s, gd, out, a.status);
+    T out[LQ], cf[L];
+    collide_gen<T, D, M, EN, PlainPull<B, K, D, M, EN>, false, true>(pp, pf, 0, mo, s, gd, out, a.status, nullptr, cf);
+#pragma unroll
+    for (int l = 0; l < L; ++l) coef[l] = cf[l].v;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
       const int dir = c0 + k;
@@ -147,9 +197,43 @@ __global__ void __launch_bounds__(128) k_adj_collide(Params<B> p, InletTables<B>
       if (dir == 0) pb_k += (double)acc;
       else if (dir == 1) pb_phi += (double)acc;
       else if (dir < 2 + NG) a.Gbar[(size_t)(dir - 2) * N + n] = acc;
-      else a.Pbar[(size_t)(dir - 2 - NG) * N + n] = acc;
+      else mbar[dir - 2 - NG] = acc;
     }
   }
+  // populations: moments' transpose plus the direct relaxation term
+  const B* mb_sa = mbar;
+  const B* mb_ja = mbar + M;
+  const B mb_sf = mbar[M + M * D];
+  const B* mb_jf = mbar + M + M * D + 1;
+  const B* mb_Pt = mbar + M + M * D + 1 + D;
+  const B mb_sg = mbar[M + M * D + 1 + D + D * D];
+  const B* mb_q = mbar + M + M * D + 1 + D + D * D + 1;
+  for_each_dir<D>([&](int i, int cx, int cy, int cz) {
+    const int cc[3] = {cx, cy, cz};
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      B v;
+      if (l < M) {
+        v = mb_sa[l];
+#pragma unroll
+        for (int b = 0; b < D; ++b) v += B(cc[b]) * mb_ja[l * D + b];
+      } else if (l == M) {
+        v = mb_sf;
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          v += B(cc[b]) * mb_jf[b];
+#pragma unroll
+          for (int c = 0; c < D; ++c) v += B(cc[b] * cc[c]) * mb_Pt[b * D + c];
+        }
+      } else {
+        v = mb_sg;
+#pragma unroll
+        for (int b = 0; b < D; ++b) v += B(cc[b]) * mb_q[b];
+      }
+      if (i != REST) v += (lam[l * Q + i] - lam[l * Q + REST]) * coef[l];
+      a.Pbar[(size_t)(l * Q + i) * N + n] = v;
+    }
+  });
   a.phibar[n] += pb_phi;
   a.kbar[n] += pb_k;
 }

@@ -223,10 +223,14 @@ struct NodeSource {
 // Collision and store of one node (runtime loop form of collide_and_store).
 // With SRC the reaction sources are added: eq:fsourceHetero to the species,
 // eqn:f_source to the momentum lattice and eqn:g_source to the energy lattice.
-template <class R, int D, int M, bool EN, class PullF, bool SRC = false>
+// With COEF, coef[l] receives the derivative of every non-rest post-collision
+// population of lattice l with respect to its own streamed population at
+// fixed moments (1 - 2 beta_a for the species, 1 - omega for the momentum and
+// energy lattices): the adjoint needs it, the step does not.
+template <class R, int D, int M, bool EN, class PullF, bool SRC = false, bool COEF = false>
 LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moments<R, D, M, EN, true>& mo,
                         const State<R, D, M>& s, const Grad<R, D, M, EN>& gr, R* __restrict__ dst, int* status,
-                        const NodeSource<R>* srcv = nullptr) {
+                        const NodeSource<R>* srcv = nullptr, R* coef = nullptr) {
   constexpr int Q = Lat<D>::Q;
   constexpr int REST = (Q - 1) / 2;
   const size_t N = p.N;
@@ -252,6 +256,12 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
   }
   const R omega = R(1) / (R(0.5) + mu / s.P);
   const R omega1 = R(1) / (R(0.5) + mu * p.inv_Pr / s.P);
+  if constexpr (COEF) {
+#pragma unroll
+    for (int a = 0; a < M; ++a) coef[a] = R(1) - R(2) * tr.beta[a];
+    coef[M] = R(1) - omega;
+    if (EN) coef[M + 1] = R(1) - omega;
+  }
   const R bulk = -p.bulk_ratio * mu + mu * (R(2) / R(D) - (EN ? s.Rg / s.cv : R(0)));
 
   // per-axis factors of the species equilibria, quasi-equilibria and

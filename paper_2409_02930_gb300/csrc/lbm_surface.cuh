@@ -64,11 +64,12 @@ __device__ __forceinline__ double ipow(double x, int n) {
 // (fluid internal energy change per unit volume, lattice units).
 //
 // Mixed precision (iterative refinement): concentrations, rates, the
-// residual F = xi - dt r(xi) and the extents are FP64; the Jacobian of F is
-// assembled and LU-factorised in FP32 (RK = float) or FP64 (RK = double)
-// and reused across iterations (simplified Newton) until the contraction of
-// the steps slows down or a step is shortened, when it is rebuilt at the
-// current iterate.  The FP64 residual fixes the root, so every variant
+// residual F = xi - dt r(xi) and the extents are FP64; the Newton systems are
+// solved in FP32 (RK = float) or FP64 (RK = double) through the species-space
+// matrix K = I - V U of the Woodbury identity (NS x NS instead of R x R),
+// whose factors are reused across iterations (simplified Newton) until the
+// contraction of the steps slows down or a step is shortened, when they are
+// rebuilt at the current iterate.  The FP64 residual fixes the root, so every variant
 // converges to the same FP64 solution.
 template <int M, class RK>
 __device__ void surface_source_dev(const MechDev& mc, double T, const double* rho_a, double phi, const double* Xs0,
@@ -82,8 +83,14 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
     xi[k] = 0.0;
   }
   const double scale = mc.a_s / phi;     // gas concentration change per extent
-  RK LU[RMAX][RMAX];
-  int swp[RMAX];
+  // J = I - U V with U = dt dr/dc (R x NS, the reactants of each step) and
+  // V = diag(scale) nu^T (NS x R); by the Woodbury identity
+  // J^-1 b = b + U K^-1 V b with K = I - V U (NS x NS), whose LU factors and U
+  // are kept while the iteration reuses them.
+  constexpr int NSX = MMAX + SMAX;
+  RK LU[NSX][NSX];
+  RK uk[RMAX][4];
+  int swp[NSX];
   bool refresh = true, converged = false;
   double prev = 0.0;
   for (int it = 0; it < 40; ++it) {
@@ -100,55 +107,67 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
       r[k] = v;
     }
     if (refresh) {
-      // J = I - dt dr/dxi: only the reactants of step k enter row k
-      for (int k = 0; k < Rn; ++k) {
-        for (int l = 0; l < Rn; ++l) LU[k][l] = (k == l) ? RK(1) : RK(0);
+      // U entries dt r_k ord / c_j of the reactants j of each step, and K = I - V U
+      for (int i = 0; i < NS; ++i)
+        for (int j = 0; j < NS; ++j) LU[i][j] = (i == j) ? RK(1) : RK(0);
+      for (int k = 0; k < Rn; ++k)
         for (int j = 0; j < mc.nre[k]; ++j) {
-          const int i = mc.ridx[k][j];
-          if (c[i] > 0.0) {
-            // d r_k / d xi_l = r_k ord / c_i dc_i/dxi_l: only the steps l in which species i takes part
-            const RK g = RK(mc.dt * r[k] * mc.rord[k][j] / c[i] * (i < M ? scale : 1.0));
-            for (int q = 0; q < mc.nsr[i]; ++q) LU[k][mc.sr_k[i][q]] -= g * sr_nu<RK>(mc, i, q);
+          const int jj = mc.ridx[k][j];
+          const RK u = c[jj] > 0.0 ? RK(mc.dt * r[k] * mc.rord[k][j] / c[jj]) : RK(0);
+          uk[k][j] = u;
+          for (int q = 0; q < mc.npart[k]; ++q) {
+            const int i = mc.pidx[k][q];
+            LU[i][jj] -= RK((i < M ? scale : 1.0) * mc.pnu[k][q]) * u;
           }
         }
-      }
-      // LU factors with partial pivoting (row swaps recorded in swp)
-      for (int cc = 0; cc < Rn; ++cc) {
+      // LU factors of K with partial pivoting (row swaps recorded in swp)
+      for (int cc = 0; cc < NS; ++cc) {
         int pv = cc;
-        for (int k = cc + 1; k < Rn; ++k)
+        for (int k = cc + 1; k < NS; ++k)
           if (fabs(LU[k][cc]) > fabs(LU[pv][cc])) pv = k;
         swp[cc] = pv;
         if (pv != cc)
-          for (int l = 0; l < Rn; ++l) {
+          for (int l = 0; l < NS; ++l) {
             RK t = LU[cc][l];
             LU[cc][l] = LU[pv][l];
             LU[pv][l] = t;
           }
         const RK inv = RK(1) / LU[cc][cc];
-        for (int k = cc + 1; k < Rn; ++k) {
+        for (int k = cc + 1; k < NS; ++k) {
           const RK f = LU[k][cc] * inv;
           LU[k][cc] = f;
-          for (int l = cc + 1; l < Rn; ++l) LU[k][l] -= f * LU[cc][l];
+          for (int l = cc + 1; l < NS; ++l) LU[k][l] -= f * LU[cc][l];
         }
       }
       refresh = false;
     }
-    // solve J dxi = -F with the stored factors
-    RK b[RMAX];
+    // solve J dxi = -F:  w = V b, K z = w, dxi = b + U z
+    RK b[RMAX], w[NSX];
     for (int k = 0; k < Rn; ++k) b[k] = RK(-(xi[k] - mc.dt * r[k]));
-    for (int cc = 0; cc < Rn; ++cc)
-      if (swp[cc] != cc) {
-        RK t = b[cc];
-        b[cc] = b[swp[cc]];
-        b[swp[cc]] = t;
+    for (int i = 0; i < NS; ++i) w[i] = RK(0);
+    for (int k = 0; k < Rn; ++k)
+      for (int q = 0; q < mc.npart[k]; ++q) {
+        const int i = mc.pidx[k][q];
+        w[i] += RK((i < M ? scale : 1.0) * mc.pnu[k][q]) * b[k];
       }
-    for (int k = 1; k < Rn; ++k)
-      for (int l = 0; l < k; ++l) b[k] -= LU[k][l] * b[l];
+    for (int cc = 0; cc < NS; ++cc)
+      if (swp[cc] != cc) {
+        RK t = w[cc];
+        w[cc] = w[swp[cc]];
+        w[swp[cc]] = t;
+      }
+    for (int k = 1; k < NS; ++k)
+      for (int l = 0; l < k; ++l) w[k] -= LU[k][l] * w[l];
+    for (int k = NS - 1; k >= 0; --k) {
+      RK s2 = w[k];
+      for (int l = k + 1; l < NS; ++l) s2 -= LU[k][l] * w[l];
+      w[k] = s2 / LU[k][k];
+    }
     double dxi[RMAX];
-    for (int k = Rn - 1; k >= 0; --k) {
-      RK s2 = b[k];
-      for (int l = k + 1; l < Rn; ++l) s2 -= LU[k][l] * RK(dxi[l]);
-      dxi[k] = (double)(s2 / LU[k][k]);
+    for (int k = 0; k < Rn; ++k) {
+      RK x = b[k];
+      for (int j = 0; j < mc.nre[k]; ++j) x += uk[k][j] * w[mc.ridx[k][j]];
+      dxi[k] = (double)x;
     }
     // steps that would take a non-negative concentration below zero are shortened
     double alpha = 1.0;

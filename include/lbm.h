@@ -193,6 +193,29 @@ size_t lbm_population_bytes(const lbm_ctx* ctx);
 int lbm_get_populations(lbm_ctx* ctx, void* buf, size_t bytes, int on_device);
 int lbm_set_populations(lbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
 
+/*
+ * lbm_save / lbm_load -- checkpoint and resume the evolving state of a
+ * context (single lattice or batch): the stored populations [L][Q][N] in the
+ * context's precision, the surface coverages [S][N] (FP64) when it has a
+ * surface mechanism, and the number of steps taken.  The image is a 128-byte
+ * header (the 8 bytes "LBMSTATE", then int64 fields: format version 1,
+ * precision, D, N, L, Q, S, steps taken, population bytes, coverage bytes)
+ * followed by the populations and the coverages.  Static fields (porosity,
+ * tortuosity, pore radius, mechanism, boundary conditions) are not saved:
+ * load into a context created from the same configuration.
+ *
+ * lbm_save: buf is a caller-owned host buffer of *bytes bytes; on return
+ * *bytes holds the image size.  buf == NULL only queries the size.
+ * Errors: LBM_ERR_ARG when bytes is NULL or the buffer is too small (*bytes
+ * then holds the size needed).
+ * lbm_load: buf is a host buffer holding an image of `bytes` bytes.  Errors:
+ * LBM_ERR_ARG when the header does not match the context (magic, version,
+ * precision, D, N, L, Q or S differ) or bytes is not the image size; the
+ * state is unchanged then.  Both calls are synchronous.
+ */
+int lbm_save(lbm_ctx* ctx, void* buf, size_t* bytes);
+int lbm_load(lbm_ctx* ctx, const void* buf, size_t bytes);
+
 /* lbm_sync -- wait for the context's stream; returns the device status. */
 int lbm_sync(lbm_ctx* ctx);
 

@@ -681,11 +681,13 @@ int lbm_step(lbm_ctx* x, int n_steps) {
   if (x->n_cases > 0) {
     int rc = x->precision == LBM_FP64 ? batch_steps(x, x->bd, n_steps) : batch_steps(x, x->bf, n_steps);
     if (rc) return rc;
+    x->steps_done += n_steps;
     n_steps = 0;
   }
   for (int s = 0; s < n_steps; ++s) {
     int rc = step_once(x);
     if (rc) return rc;
+    ++x->steps_done;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(x, e, "step launch");
@@ -870,6 +872,64 @@ int lbm_set_populations(lbm_ctx* x, const void* buf, size_t bytes, int on_device
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, x->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
   return e == cudaSuccess ? LBM_OK : cuda_fail(x, e, "population copy");
+}
+
+// checkpoint image: 128-byte header, populations, coverages
+namespace {
+constexpr size_t kImageHeader = 128;
+constexpr long long kImageVersion = 1;
+size_t coverage_bytes(const lbm_ctx* x) { return x->S > 0 ? (size_t)x->S * x->N * sizeof(double) : 0; }
+void image_header(const lbm_ctx* x, long long* h /* [10] */) {
+  h[0] = kImageVersion; h[1] = x->precision; h[2] = x->D; h[3] = x->N; h[4] = x->L; h[5] = x->Q;
+  h[6] = x->S; h[7] = x->steps_done; h[8] = (long long)lbm_population_bytes(x); h[9] = (long long)coverage_bytes(x);
+}
+}  // namespace
+
+int lbm_save(lbm_ctx* x, void* buf, size_t* bytes) {
+  if (!x || !bytes) return LBM_ERR_ARG;
+  const size_t pb = lbm_population_bytes(x), cb = coverage_bytes(x);
+  const size_t need = kImageHeader + pb + cb;
+  if (!buf) {
+    *bytes = need;
+    return LBM_OK;
+  }
+  if (*bytes < need) {
+    *bytes = need;
+    return fail(x, LBM_ERR_ARG, "checkpoint buffer too small");
+  }
+  unsigned char* out = static_cast<unsigned char*>(buf);
+  std::memset(out, 0, kImageHeader);
+  std::memcpy(out, "LBMSTATE", 8);
+  long long h[10];
+  image_header(x, h);
+  std::memcpy(out + 8, h, sizeof(h));
+  cudaError_t e = cudaMemcpyAsync(out + kImageHeader, x->pops[x->cur], pb, cudaMemcpyDeviceToHost, x->stream);
+  if (e == cudaSuccess && cb)
+    e = cudaMemcpyAsync(out + kImageHeader + pb, x->Xs[x->xs_cur], cb, cudaMemcpyDeviceToHost, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  if (e != cudaSuccess) return cuda_fail(x, e, "checkpoint copy");
+  *bytes = need;
+  return LBM_OK;
+}
+
+int lbm_load(lbm_ctx* x, const void* buf, size_t bytes) {
+  if (!x || !buf) return LBM_ERR_ARG;
+  const size_t pb = lbm_population_bytes(x), cb = coverage_bytes(x);
+  if (bytes != kImageHeader + pb + cb) return fail(x, LBM_ERR_ARG, "checkpoint image size does not match the context");
+  const unsigned char* in = static_cast<const unsigned char*>(buf);
+  if (std::memcmp(in, "LBMSTATE", 8) != 0) return fail(x, LBM_ERR_ARG, "not a checkpoint image");
+  long long h[10], mine[10];
+  std::memcpy(h, in + 8, sizeof(h));
+  image_header(x, mine);
+  for (int k = 0; k < 10; ++k)
+    if (k != 7 && h[k] != mine[k]) return fail(x, LBM_ERR_ARG, "checkpoint image does not match the context");
+  cudaError_t e = cudaMemcpyAsync(x->pops[x->cur], in + kImageHeader, pb, cudaMemcpyHostToDevice, x->stream);
+  if (e == cudaSuccess && cb)
+    e = cudaMemcpyAsync(x->Xs[x->xs_cur], in + kImageHeader + pb, cb, cudaMemcpyHostToDevice, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  if (e != cudaSuccess) return cuda_fail(x, e, "checkpoint copy");
+  x->steps_done = h[7];
+  return LBM_OK;
 }
 
 int lbm_sync(lbm_ctx* x) {

@@ -37,6 +37,7 @@ struct lbm_ctx {
   std::vector<int> ev_kind;
   size_t ev_used;
   int variant;                       // < 0: two-pass form; >= 0: fused tile shape
+  long long steps_done;              // steps taken through lbm_step (checkpoint images carry it)
   // surface mechanism (S > 0): coverages (ping-pong), per-node sources, mechanism table
   double* Xs[2];
   int xs_cur;

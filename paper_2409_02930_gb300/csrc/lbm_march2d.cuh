@@ -7,7 +7,9 @@
 // addresses already contain the periodic wrap and the bounce-back rule), two
 // rows ahead of their use, so the HBM latency is covered by the compute of
 // the rows in between and no register holds a population while it is in
-// flight.  For each row the block first computes the gradient inputs
+// flight; the porosity (and the fixed temperature of isothermal lattices) of
+// every node travels the same way, so the loop issues no plain global load.
+// For each row the block first computes the gradient inputs
 // (u, Pi_alpha, Y_a) of all its columns into a three-row shared ring, then
 // collides the interior columns of the previous row from shared memory.
 // Columns next to a reservoir face take the global-memory path (their
@@ -40,9 +42,12 @@ struct SmemPull {
 };
 
 // PD rows are prefetched ahead; PD + 2 row buffers are in use at a time
+// (the static fields of each row -- porosity, and the fixed temperature of
+// isothermal lattices -- travel with its populations)
 template <class R, int M, bool EN, int TX, int PD>
 constexpr size_t march2d_smem_bytes() {
-  return sizeof(R) * (size_t)TX * ((PD + 2) * (M + 1 + (EN ? 1 : 0)) * 9 + 3 * (4 + (EN ? M : 0)));
+  return sizeof(R) * (size_t)TX *
+         ((PD + 2) * ((M + 1 + (EN ? 1 : 0)) * 9 + (EN ? 1 : 2)) + 3 * (4 + (EN ? M : 0)));
 }
 
 // INLET = false compiles the kernel without the reservoir-column path (for
@@ -54,9 +59,11 @@ __global__ void __launch_bounds__(TX, MINB) k_march2d(Params<R> p, InletTables<R
   constexpr int NL = M + 1 + (EN ? 1 : 0);
   constexpr int NF = 2 * D + (EN ? M : 0);
   constexpr int NBUF = PD + 2;
+  constexpr int NS = EN ? 1 : 2;                     // static fields per node: phi (, Tfix)
   extern __shared__ unsigned char smem_raw[];
   R* P = reinterpret_cast<R*>(smem_raw);           // [NBUF][NL*Q][TX]
   R* ring = P + (size_t)NBUF * NL * Q * TX;         // [3][NF][TX]
+  R* SF = ring + (size_t)3 * NF * TX;               // [NBUF][NS][TX]
 
   const int t = threadIdx.x;
   const int x0 = blockIdx.x * (TX - 2);
@@ -77,6 +84,9 @@ __global__ void __launch_bounds__(TX, MINB) k_march2d(Params<R> p, InletTables<R
     if (!slow) {
       const int y = modp(row, p.ny);
       R* dcol = P + (size_t)buf_of(row) * NL * Q * TX + t;
+      R* scol = SF + (size_t)buf_of(row) * NS * TX + t;
+      cp_async_ca<sizeof(R)>(scol, a.phi + xm + p.nx * y);
+      if (!EN) cp_async_ca<sizeof(R)>(scol + TX, a.Tfix + xm + p.nx * y);
 #pragma unroll 1
       for (int cy = -1; cy <= 1; ++cy) {
         const int sy = wrapi(y - cy, p.ny);
@@ -124,8 +134,9 @@ __global__ void __launch_bounds__(TX, MINB) k_march2d(Params<R> p, InletTables<R
         SmemPull<R, D> pf{P + (size_t)buf_of(s) * NL * Q * TX + t, TX};
         moments_gen<R, D, M, EN, false>(pf, mo);
       }
+      const R* sf = SF + (size_t)buf_of(s) * NS * TX + t;
       State<R, D, M> st;
-      st.template from_moments<EN, false>(p, mo, a.phi[n], EN ? R(0) : a.Tfix[n]);
+      st.template from_moments<EN, false>(p, mo, slow ? a.phi[n] : sf[0], EN ? R(0) : (slow ? a.Tfix[n] : sf[TX]));
       R* rs = ring + (size_t)slot_of(s) * NF * TX + t;
 #pragma unroll
       for (int b = 0; b < D; ++b) {
@@ -156,8 +167,10 @@ __global__ void __launch_bounds__(TX, MINB) k_march2d(Params<R> p, InletTables<R
         SmemPull<R, D> pf{P + (size_t)buf_of(y) * NL * Q * TX + t, TX};
         moments_gen<R, D, M, EN, true>(pf, mo);
       }
+      // this thread's ring column is its collide column (xm == xt here)
+      const R* sf = SF + (size_t)buf_of(y) * NS * TX + t;
       State<R, D, M> st;
-      st.template from_moments<EN, true>(p, mo, a.phi[n], EN ? R(0) : a.Tfix[n]);
+      st.template from_moments<EN, true>(p, mo, slow ? a.phi[n] : sf[0], EN ? R(0) : (slow ? a.Tfix[n] : sf[TX]));
       Grad<R, D, M, EN> gr;
       gr.divu = R(0);
 #pragma unroll

@@ -112,6 +112,10 @@ def load(path: str = LIB_PATH):
     L.lbm_set_timing.restype = ctypes.c_int
     L.lbm_get_timing.argtypes = [vp, _dp, ctypes.POINTER(ctypes.c_longlong)]
     L.lbm_get_timing.restype = ctypes.c_int
+    L.lbm_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
+    L.lbm_save.restype = ctypes.c_int
+    L.lbm_load.argtypes = [vp, vp, ctypes.c_size_t]
+    L.lbm_load.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -288,6 +292,19 @@ class Lattice:
         dt = np.float64 if self.precision == LBM_FP64 else np.float32
         a = np.ascontiguousarray(np.asarray(p, dtype=dt)).reshape(self.L, self.Q, self.N)
         self._check(load().lbm_set_populations(self._h, a.ctypes.data, a.nbytes, 0), "lbm_set_populations")
+
+    def save(self) -> bytes:
+        """Checkpoint image of the evolving state (populations, coverages, steps taken)."""
+        n = ctypes.c_size_t(0)
+        self._check(load().lbm_save(self._h, None, ctypes.byref(n)), "lbm_save")
+        buf = np.empty(n.value, dtype=np.uint8)
+        self._check(load().lbm_save(self._h, buf.ctypes.data, ctypes.byref(n)), "lbm_save")
+        return buf.tobytes()
+
+    def load_state(self, image: bytes):
+        """Resume from an image written by save() of a context with the same configuration."""
+        buf = np.frombuffer(image, dtype=np.uint8)
+        self._check(load().lbm_load(self._h, buf.ctypes.data, buf.nbytes), "lbm_load")
 
     def close(self):
         h = getattr(self, "_h", None)

@@ -516,6 +516,7 @@ static int read_status(lbm_ctx* x) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
   if (e != cudaSuccess) return cuda_fail(x, e, "status read");
   if (st & 1) return fail(x, LBM_ERR_NUMERIC, "non-finite or non-positive density or temperature");
+  if (st & lbm::kStatusTimeout) return fail(x, LBM_ERR_TIMEOUT, "a bounded device wait gave up");
   return LBM_OK;
 }
 

@@ -61,7 +61,33 @@ struct Launch {
         static bool done[2] = {false, false};
         if (configure(kern, smem, done[inlet ? 1 : 0])) return -1;
         dim3 g((p.nx + TX - 3) / (TX - 2), (p.ny + SEG - 1) / SEG, 1);
-        kern<<<g, TX, smem, s>>>(p, it, a);
+        kern<<<g, TX, smem, s>>>(p, it, a, TmaMaps{});
+        return 0;
+      }
+    }
+  }
+  // the same march with each row staged by bulk tensor copies (TMA); lattices
+  // whose rows are not a multiple of 16 bytes take the cp.async form
+  template <int TX, int SEG, int MINB, int PD>
+  static int march2d_tma(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, cudaStream_t s) {
+    if constexpr (D != 2) {
+      return -1;
+    } else {
+      using LB = RowBoxLayout<R, M, EN, TX, PD>;
+      constexpr size_t smem = LB::bytes();
+      if constexpr (smem > kMaxSmem) {
+        return -1;
+      } else {
+        TmaMaps tm;
+        if (!encode_row_maps<R>(tm, a.src, a.phi, EN ? nullptr : a.Tfix, p.nx, p.ny, Lat<D>::Q, LB::NL, LB::W))
+          return march2d<TX, SEG, MINB, PD>(p, it, a, s);
+        const bool inlet = p.bc_lo == BC_INLET || p.bc_hi == BC_INLET;
+        auto kern = inlet ? k_march2d<R, M, EN, TX, SEG, MINB, PD, true, true>
+                          : k_march2d<R, M, EN, TX, SEG, MINB, PD, false, true>;
+        static bool done[2] = {false, false};
+        if (configure(kern, smem, done[inlet ? 1 : 0])) return -1;
+        dim3 g((p.nx + TX - 3) / (TX - 2), (p.ny + SEG - 1) / SEG, 1);
+        kern<<<g, TX, smem, s>>>(p, it, a, tm);
         return 0;
       }
     }
@@ -93,6 +119,8 @@ struct Launch {
         case 5: return fused_tile<32, 1, 8>(p, it, a, s);
         case 6: return staged<64>(p, it, a, s);
         case 7: return staged<128>(p, it, a, s);
+        case 8: return march2d_tma<32, 8, 1, 1>(p, it, a, s);
+        case 9: return march2d_tma<64, 8, 1, 1>(p, it, a, s);
         default: return -1;
       }
     } else {
@@ -106,7 +134,7 @@ struct Launch {
       }
     }
   }
-  static constexpr int n_variants = (D == 2) ? 8 : 5;
+  static constexpr int n_variants = (D == 2) ? 10 : 5;
   static void init(const Params<R>& p, const double* X, const double* T, const double* P, const double* U,
                    double cvel, double RU, R* dst, const R* phi, cudaStream_t s) {
     k_init<R, D, M, EN><<<grid(p.N), 256, 0, s>>>(p, X, T, P, U, cvel, RU, dst, phi);

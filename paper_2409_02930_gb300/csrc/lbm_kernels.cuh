@@ -14,8 +14,11 @@ struct StepArgs {
   const R* __restrict__ phi;     // porosity [N]
   const R* __restrict__ Tfix;    // fixed temperature [N] (isothermal lattices)
   R* __restrict__ mac;           // macro fields for the gradients [2D+M][N]
-  int* status;                   // bit 0: non-finite / non-positive density, bit 1: FP64 solve used
+  int* status;                   // bit 0: non-finite / non-positive density, bit 1: FP64 solve used,
+                                 // bit 2: surface Newton not converged, bit 3: a bounded wait gave up
 };
+
+constexpr int kStatusTimeout = 8;   // status bit 3: a bounded device wait gave up
 
 LBM_HD void flag(int* status, int bit) {
 #ifdef __CUDA_ARCH__

@@ -24,16 +24,23 @@ def header(image):
     return struct.unpack("<10q", image[8:88])
 
 
+def flat(p):
+    # a batch returns one population array per case
+    if isinstance(p, list):
+        return np.concatenate([x.reshape(-1) for x in p])
+    return p.reshape(-1)
+
+
 def resume_matches(make, n1, n2):
     a = make()
     a.step(n1)
     image = a.save()
     a.step(n2)
-    pa = a.populations()
+    pa = flat(a.populations())
     b = make()
     b.load_state(image)
     b.step(n2)
-    pb = b.populations()
+    pb = flat(b.populations())
     assert np.array_equal(pa.view(np.uint8), pb.view(np.uint8))
     return a, b, image
 

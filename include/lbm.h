@@ -237,10 +237,19 @@ int lbm_get_timing(lbm_ctx* ctx, double* ms_by_kind /* [3] */, long long* launch
 /*
  * Kernel forms.  Variant -1 is the two-pass form (a macro-field pass writes
  * u, Pi and Y_a to a device buffer, then the node update reads it); variants
- * 0 .. lbm_variant_count()-1 are the fused single-kernel step with different
- * tile shapes (the macro fields of each tile's halo are recomputed into
- * shared memory).  Every form computes the same step.  New contexts use
- * variant 0.  lbm_autotune times every form for `steps` steps on the
+ * 0 .. lbm_variant_count()-1 are single-launch or staged forms with
+ * different tile shapes.  D2Q9: 0-4 the pipelined row march with per-thread
+ * asynchronous copies, 5 a fused halo tile, 6-7 the staged two-pass form,
+ * 8-9 the row march staged by bulk tensor copies (TMA; on lattices whose
+ * rows are not a multiple of 16 bytes they run the per-thread-copy march of
+ * the same tile shape, variants 2 and 0).
+ * D3Q27: 0-2 fused halo tiles, 3-4 the staged two-pass form.  Every form
+ * computes the same step (the gradient stencil is summed in different
+ * orders, so the forms agree to rounding).  New contexts use variant 3 in
+ * 3-D and, in 2-D, variant 8 on lattices of at least 2^18 nodes without a
+ * reservoir face, else the two-pass form; batches use variant 2.  The adjoint's
+ * forward and recompute steps use the context's form.  lbm_autotune times
+ * every form for `steps` steps on the
  * current state, restores the state, selects the fastest form and writes its
  * index to *best (may be NULL).  Errors: LBM_ERR_ARG (unknown variant,
  * steps < 1), LBM_ERR_ALLOC.

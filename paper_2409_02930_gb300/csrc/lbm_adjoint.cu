@@ -59,8 +59,10 @@ int run_adjoint(lbm_ctx* x, const lbm::Ops<B>& ops, const lbm::Params<B>& p, con
   B* mac = (B*)x->mac;
   const B* phi = (const B*)x->phi;
   const B* Tfix = (const B*)x->Tfix;
+  // forward and recompute steps in the context's kernel form
   auto step = [&](const B* src, B* dst) {
     lbm::StepArgs<B> a{src, dst, phi, Tfix, mac, x->status};
+    if (x->variant >= 0 && ops.fused(p, it, a, x->variant, s) == 0) return;
     ops.macro(p, it, a, s);
     ops.collide(p, it, a, s);
   };

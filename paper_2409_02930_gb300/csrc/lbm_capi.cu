@@ -266,7 +266,12 @@ int lbm_create(lbm_ctx** out, const lbm_config* c) {
   x->S = c->S;
   x->stream = (cudaStream_t)c->stream;
   x->cur = 0;
-  x->variant = 0;
+  // default form: the staged two-pass form in 3-D; in 2-D the TMA row march
+  // where it fills the GPU (one 32-column block per 8 rows: 1152 blocks at
+  // 512 x 512) and no x face is a reservoir (reservoir columns take a
+  // global-memory path that sets the march's pace), else the two-pass form
+  const bool reservoir = c->bc_lo == LBM_BC_INLET || c->bc_hi == LBM_BC_INLET;
+  x->variant = c->nz > 1 ? 3 : ((!reservoir && x->N >= (1 << 18)) ? 8 : -1);
 
   bool ok = (x->precision == LBM_FP64)
                 ? (x->D == 2 ? lbm::get_ops_f64_2d(x->M, x->energy, &x->od) : lbm::get_ops_f64_3d(x->M, x->energy, &x->od))

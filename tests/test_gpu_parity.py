@@ -59,6 +59,8 @@ CASES = {
     "slab_64x40_energy": lambda: W.slab(nx=64, ny=40, steps=300),
     "slab_48x32_inlet": lambda: W.adjoint_slab(nx=48, ny=32, steps=200),
     "slab_40x24_bounceback": lambda: bounceback_slab(),
+    # rows of 45 x 8 bytes: no tensor map, the TMA forms fall back to per-thread copies
+    "slab_45x24_odd_width": lambda: W.slab(nx=45, ny=24, steps=200),
     "slab3d_m3": lambda: small_3d_m3(),
     "anode3d_m6": lambda: small_3d(),
 }

@@ -216,6 +216,25 @@ int lbm_set_populations(lbm_ctx* ctx, const void* buf, size_t bytes, int on_devi
 int lbm_save(lbm_ctx* ctx, void* buf, size_t* bytes);
 int lbm_load(lbm_ctx* ctx, const void* buf, size_t bytes);
 
+/*
+ * lbm_step_host -- streaming form for states that live in host memory: copies
+ * the state in_host ([L][Q][N] populations in the context's precision, the
+ * layout of lbm_get_populations) to the device, advances it n_steps with the
+ * context's kernel form and parameters, and copies the result to out_host.
+ * The context's own state (lbm_step, lbm_get_populations) is not touched.
+ * Asynchronous: the call only enqueues.  The upload runs on an upload
+ * stream, the steps on the context's stream and the download on a download
+ * stream; alternate calls use two different pairs of device state slots, so
+ * the upload of one call overlaps the steps and the download of the one
+ * before.  in_host must stay unmodified, and out_host must not be read,
+ * until lbm_sync returns (which waits for every stream of the context).  Use
+ * page-locked host memory for the copies to overlap.  The first call
+ * allocates four state slots.  Errors: LBM_ERR_ARG (null buffers, n_steps <
+ * 0), LBM_ERR_STATE (batched contexts and lattices with a surface mechanism,
+ * whose state is more than the populations), LBM_ERR_ALLOC, LBM_ERR_CUDA.
+ */
+int lbm_step_host(lbm_ctx* ctx, const void* in_host, void* out_host, int n_steps);
+
 /* lbm_sync -- wait for the context's stream; returns the device status. */
 int lbm_sync(lbm_ctx* ctx);
 

@@ -938,8 +938,83 @@ int lbm_load(lbm_ctx* x, const void* buf, size_t bytes) {
   return LBM_OK;
 }
 
+static void release_streaming(lbm_ctx* x) {
+  if (x->d2h) cudaStreamSynchronize(x->d2h);
+  if (x->h2d) cudaStreamSynchronize(x->h2d);
+  for (int k = 0; k < 4; ++k)
+    if (x->hslot[k]) cudaFree(x->hslot[k]), x->hslot[k] = nullptr;
+  for (int k = 0; k < 2; ++k) {
+    if (x->ev_in[k]) cudaEventDestroy(x->ev_in[k]), x->ev_in[k] = nullptr;
+    if (x->ev_done[k]) cudaEventDestroy(x->ev_done[k]), x->ev_done[k] = nullptr;
+    if (x->ev_free[k]) cudaEventDestroy(x->ev_free[k]), x->ev_free[k] = nullptr;
+    x->free_recorded[k] = false;
+  }
+  if (x->h2d) cudaStreamDestroy(x->h2d), x->h2d = nullptr;
+  if (x->d2h) cudaStreamDestroy(x->d2h), x->d2h = nullptr;
+}
+
+int lbm_step_host(lbm_ctx* x, const void* in_host, void* out_host, int n_steps) {
+  if (!x) return LBM_ERR_ARG;
+  if (!in_host || !out_host || n_steps < 0) return fail(x, LBM_ERR_ARG, "lbm_step_host: null buffer or negative step count");
+  if (x->n_cases > 0 || x->S > 0)
+    return fail(x, LBM_ERR_STATE, "lbm_step_host: single lattices without a surface mechanism only");
+  const size_t pb = lbm_population_bytes(x);
+  cudaError_t e = cudaSuccess;
+  if (!x->h2d) {
+    e = cudaStreamCreateWithFlags(&x->h2d, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x->d2h, cudaStreamNonBlocking);
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) {
+      e = cudaEventCreateWithFlags(&x->ev_in[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->ev_done[k], cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x->ev_free[k], cudaEventDisableTiming);
+    }
+    for (int k = 0; k < 4 && e == cudaSuccess; ++k) e = cudaMalloc(&x->hslot[k], pb);
+    if (e != cudaSuccess) {
+      release_streaming(x);
+      return fail(x, LBM_ERR_ALLOC, std::string("lbm_step_host: stream or slot allocation failed: ") +
+                                        cudaGetErrorString(e));
+    }
+  }
+  const int P = (int)(x->hcall & 1);
+  void* sa = x->hslot[2 * P];
+  void* sb = x->hslot[2 * P + 1];
+  // upload once the download of the pair's previous call has finished
+  if (x->free_recorded[P]) e = cudaStreamWaitEvent(x->h2d, x->ev_free[P], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(sa, in_host, pb, cudaMemcpyHostToDevice, x->h2d);
+  if (e == cudaSuccess) e = cudaEventRecord(x->ev_in[P], x->h2d);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(x->stream, x->ev_in[P], 0);
+  if (e != cudaSuccess) return cuda_fail(x, e, "lbm_step_host upload");
+  // the steps ping-pong between the pair's slots on the context's stream
+  void* keep0 = x->pops[0];
+  void* keep1 = x->pops[1];
+  const int keep_cur = x->cur;
+  x->pops[0] = sa;
+  x->pops[1] = sb;
+  x->cur = 0;
+  int rc = LBM_OK;
+  for (int s = 0; s < n_steps && rc == LBM_OK; ++s) rc = step_once(x);
+  void* result = x->pops[x->cur];
+  x->pops[0] = keep0;
+  x->pops[1] = keep1;
+  x->cur = keep_cur;
+  if (rc != LBM_OK) return rc;
+  e = cudaEventRecord(x->ev_done[P], x->stream);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(x->d2h, x->ev_done[P], 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, result, pb, cudaMemcpyDeviceToHost, x->d2h);
+  if (e == cudaSuccess) e = cudaEventRecord(x->ev_free[P], x->d2h);
+  if (e != cudaSuccess) return cuda_fail(x, e, "lbm_step_host download");
+  x->free_recorded[P] = true;
+  ++x->hcall;
+  return LBM_OK;
+}
+
 int lbm_sync(lbm_ctx* x) {
   if (!x) return LBM_ERR_ARG;
+  if (x->h2d) {
+    cudaError_t e = cudaStreamSynchronize(x->h2d);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->d2h);
+    if (e != cudaSuccess) return cuda_fail(x, e, "copy stream synchronisation");
+  }
   return read_status(x);
 }
 
@@ -973,6 +1048,7 @@ int lbm_info(const lbm_ctx* x, double* out5) {
 void lbm_destroy(lbm_ctx* x) {
   if (!x) return;
   cudaStreamSynchronize(x->stream);
+  release_streaming(x);
   void* bufs[15] = {x->pops[0], x->pops[1], x->phi, x->Tfix, x->mac, x->status, x->scratch_out,
                    x->Xs[0], x->Xs[1], x->rsrc, x->mech, x->init_X, x->init_T, x->init_P, x->init_U};
   for (void* b : bufs)

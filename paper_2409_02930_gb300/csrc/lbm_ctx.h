@@ -38,6 +38,14 @@ struct lbm_ctx {
   size_t ev_used;
   int variant;                       // < 0: two-pass form; >= 0: fused tile shape
   long long steps_done;              // steps taken through lbm_step (checkpoint images carry it)
+  // streaming steps on host-resident states (lbm_step_host): two pairs of
+  // device state slots used by alternate calls, an upload and a download
+  // stream, and per pair the events ordering upload -> steps -> download
+  void* hslot[4];
+  cudaStream_t h2d, d2h;
+  cudaEvent_t ev_in[2], ev_done[2], ev_free[2];
+  bool free_recorded[2];
+  long long hcall;
   // surface mechanism (S > 0): coverages (ping-pong), per-node sources, mechanism table
   double* Xs[2];
   int xs_cur;

@@ -112,6 +112,8 @@ def load(path: str = LIB_PATH):
     L.lbm_set_timing.restype = ctypes.c_int
     L.lbm_get_timing.argtypes = [vp, _dp, ctypes.POINTER(ctypes.c_longlong)]
     L.lbm_get_timing.restype = ctypes.c_int
+    L.lbm_step_host.argtypes = [vp, vp, vp, ctypes.c_int]
+    L.lbm_step_host.restype = ctypes.c_int
     L.lbm_save.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_size_t)]
     L.lbm_save.restype = ctypes.c_int
     L.lbm_load.argtypes = [vp, vp, ctypes.c_size_t]
@@ -122,6 +124,15 @@ def load(path: str = LIB_PATH):
 
 def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(np.asarray(a, dtype=np.float64)).reshape(-1)
+
+
+def _addr(buf) -> int:
+    """Address of a host buffer: numpy array, torch tensor or integer."""
+    if isinstance(buf, int):
+        return buf
+    if isinstance(buf, np.ndarray):
+        return buf.ctypes.data
+    return int(buf.data_ptr())
 
 
 def _current_stream():
@@ -292,6 +303,13 @@ class Lattice:
         dt = np.float64 if self.precision == LBM_FP64 else np.float32
         a = np.ascontiguousarray(np.asarray(p, dtype=dt)).reshape(self.L, self.Q, self.N)
         self._check(load().lbm_set_populations(self._h, a.ctypes.data, a.nbytes, 0), "lbm_set_populations")
+
+    def step_host(self, src, dst, n: int = 1):
+        """Streaming step on a host-resident state (lbm_step_host): src and dst
+        are host buffers of population_bytes() (numpy arrays, page-locked torch
+        tensors or addresses).  Asynchronous: keep both alive and call sync()
+        before reading dst."""
+        self._check(load().lbm_step_host(self._h, _addr(src), _addr(dst), n), "lbm_step_host")
 
     def save(self) -> bytes:
         """Checkpoint image of the evolving state (populations, coverages, steps taken)."""

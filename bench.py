@@ -101,6 +101,28 @@ def other_forms(stream, torch, lbm):
         "value": wl.N * wl.L * n_adj / el / 1e6, "unit": UNIT,
         "note": "forward with checkpoints + recomputation + reverse sweep per step (wall clock)"}
     g.close()
+    # 3-D anode without reactions (D3Q27, six species, energy): 200 timed
+    # steps after 20 warm-up steps in the default form (staged two-pass), and
+    # the plain FP64 step
+    wl = W.anode3d()
+    g = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
+    g.step(20)
+    ms = timed(g.step, 200) / 200
+    hbm_peak, _ = peaks()
+    alg = algorithmic_bytes_per_node(wl, 4) * wl.N
+    out["anode_256x128x128_fp32"] = {
+        "ms_per_step": ms, "nodes": wl.N, "variant": g.variant(),
+        "value": wl.N * wl.L * 1e3 / ms / 1e6, "unit": UNIT,
+        "achieved_gbs": alg / (ms / 1e3) / 1e9, "frac_of_measured_hbm": alg / (ms / 1e3) / 1e9 / hbm_peak,
+        "note": "whole step (macro-field pass + node update) against the algorithmic bytes"}
+    g.close()
+    g = lbm.Lattice(wl, precision=lbm.LBM_FP64, stream=sp)
+    g.step(1)
+    ms = timed(g.step, 3) / 3
+    out["anode_256x128x128_fp64"] = {
+        "ms_per_step": ms, "nodes": wl.N, "value": wl.N * wl.L * 1e3 / ms / 1e6, "unit": UNIT,
+        "bound": "fp64 alu"}
+    g.close()
     # reactive 3-D anode: surface source in mixed precision
     wl = W.anode3d_reactive(steps=5)
     g = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)

@@ -262,9 +262,10 @@ int lbm_get_timing(lbm_ctx* ctx, double* ms_by_kind /* [3] */, long long* launch
  * 8-9 the row march staged by bulk tensor copies (TMA; on lattices whose
  * rows are not a multiple of 16 bytes they run the per-thread-copy march of
  * the same tile shape, variants 2 and 0).
- * D3Q27: 0-2 fused halo tiles, 3-4 the staged two-pass form.  Every form
+ * D3Q27: 0-2 fused halo tiles, 3-4 the staged two-pass form, 5 the staged
+ * form with the gradient inputs computed in a pass of their own.  Every form
  * computes the same step (the gradient stencil is summed in different
- * orders, so the forms agree to rounding).  New contexts use variant 3 in
+ * orders, so the forms agree to rounding).  New contexts use variant 5 in
  * 3-D and, in 2-D, variant 8 on lattices of at least 2^18 nodes without a
  * reservoir face, else the two-pass form; batches use variant 2.  The adjoint's
  * forward and recompute steps use the context's form.  lbm_autotune times

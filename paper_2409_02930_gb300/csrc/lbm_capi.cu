@@ -266,12 +266,12 @@ int lbm_create(lbm_ctx** out, const lbm_config* c) {
   x->S = c->S;
   x->stream = (cudaStream_t)c->stream;
   x->cur = 0;
-  // default form: the staged two-pass form in 3-D; in 2-D the TMA row march
+  // default form: in 3-D the staged form with a gradient pass; in 2-D the TMA row march
   // where it fills the GPU (one 32-column block per 8 rows: 1152 blocks at
   // 512 x 512) and no x face is a reservoir (reservoir columns take a
   // global-memory path that sets the march's pace), else the two-pass form
   const bool reservoir = c->bc_lo == LBM_BC_INLET || c->bc_hi == LBM_BC_INLET;
-  x->variant = c->nz > 1 ? 3 : ((!reservoir && x->N >= (1 << 18)) ? 8 : -1);
+  x->variant = c->nz > 1 ? 5 : ((!reservoir && x->N >= (1 << 18)) ? 8 : -1);
 
   bool ok = (x->precision == LBM_FP64)
                 ? (x->D == 2 ? lbm::get_ops_f64_2d(x->M, x->energy, &x->od) : lbm::get_ops_f64_3d(x->M, x->energy, &x->od))
@@ -288,7 +288,10 @@ int lbm_create(lbm_ctx** out, const lbm_config* c) {
   const size_t rs = real_size(x);
   const size_t pop_bytes = (size_t)x->L * x->Q * N * rs;
   void* ptrs[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-  size_t sizes[6] = {pop_bytes, pop_bytes, N * rs, N * rs, (size_t)(2 * x->D + M) * N * rs, 64};
+  // macro scratch: u, Pi, Y_a, and in 3-D the gradient inputs of the staged
+  // form with a gradient pass (1 + D + M D more fields)
+  const size_t mac_fields = (size_t)(2 * x->D + M) + (x->D == 3 ? (size_t)(1 + x->D + M * x->D) : 0);
+  size_t sizes[6] = {pop_bytes, pop_bytes, N * rs, N * rs, mac_fields * N * rs, 64};
   for (int k = 0; k < 6; ++k) {
     e = cudaMalloc(&ptrs[k], sizes[k]);
     if (e != cudaSuccess) {

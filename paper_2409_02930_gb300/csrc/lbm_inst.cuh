@@ -108,6 +108,24 @@ struct Launch {
       return 0;
     }
   }
+  // the staged form with the gradient inputs computed once per node in a pass
+  // of their own (3-D; the macro buffer holds them after the macro fields)
+  template <int TB>
+  static int staged_grad(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, cudaStream_t s) {
+    constexpr size_t smem = sizeof(R) * (size_t)n_pops<R, D, M, EN>() * TB;
+    if constexpr (D != 3 || smem > kMaxSmem) {
+      return -1;
+    } else {
+      auto kern = k_collide_staged_g<R, D, M, EN, TB>;
+      auto kmac = k_macro_staged<R, D, M, EN, TB>;
+      static bool done = false, done_mac = false;
+      if (configure(kern, smem, done) || configure(kmac, smem, done_mac)) return -1;
+      kmac<<<(p.N + TB - 1) / TB, TB, smem, s>>>(p, it, a);
+      k_grad<R, D, M, EN><<<(p.N + 255) / 256, 256, 0, s>>>(p, a);
+      kern<<<(p.N + TB - 1) / TB, TB, smem, s>>>(p, it, a);
+      return 0;
+    }
+  }
   static int fused(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, int v, cudaStream_t s) {
     if constexpr (D == 2) {
       switch (v) {
@@ -130,11 +148,12 @@ struct Launch {
         case 2: return fused_tile<32, 4, 8>(p, it, a, s);
         case 3: return staged<64>(p, it, a, s);
         case 4: return staged<32>(p, it, a, s);
+        case 5: return staged_grad<64>(p, it, a, s);
         default: return -1;
       }
     }
   }
-  static constexpr int n_variants = (D == 2) ? 10 : 5;
+  static constexpr int n_variants = (D == 2) ? 10 : 6;
   static void init(const Params<R>& p, const double* X, const double* T, const double* P, const double* U,
                    double cvel, double RU, R* dst, const R* phi, cudaStream_t s) {
     k_init<R, D, M, EN><<<grid(p.N), 256, 0, s>>>(p, X, T, P, U, cvel, RU, dst, phi);

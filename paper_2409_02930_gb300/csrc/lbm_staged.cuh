@@ -105,6 +105,77 @@ __device__ __forceinline__ void collide_staged_node(const Params<R>& p, const In
   collide_gen<R, D, M, EN>(p, pf, n, mo, s, gr, a.dst, a.status);
 }
 
+// Gradient inputs of every node (divu, dPi_b and, with energy, dY_a,b) in a
+// pass of their own, written after the macro fields at
+// mac + (2D + M) N as [1 + D + M D][N]: the node update then reads NG
+// coalesced values instead of gathering the macro fields of its 26 (8)
+// neighbours.  Same stencil code and order as the gathering form.
+template <int D, int M, bool EN>
+constexpr int n_grad_fields() {
+  return 1 + D + (EN ? M * D : 0);
+}
+
+template <class R, int D, int M, bool EN>
+__global__ void __launch_bounds__(256) k_grad(Params<R> p, StepArgs<R> a) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= p.N) return;
+  int x, y, z;
+  node_xyz<R, D>(p, n, x, y, z);
+  const R* __restrict__ mac = a.mac;
+  const size_t N = p.N;
+  Grad<R, D, M, EN> gr;
+  gr.compute(p, x, y, z, [&](int k, int nb) { return mac[(size_t)k * N + nb]; });
+  R* g = a.mac + (size_t)(2 * D + M) * N;
+  g[n] = gr.divu;
+#pragma unroll
+  for (int b = 0; b < D; ++b) g[(size_t)(1 + b) * N + n] = gr.dPi[b];
+  if (EN) {
+#pragma unroll
+    for (int k = 0; k < M; ++k)
+#pragma unroll
+      for (int b = 0; b < D; ++b) g[(size_t)(1 + D + k * D + b) * N + n] = gr.dY[k][b];
+  }
+}
+
+// Node update of node n from its staged populations and the gradient inputs
+// of the gradient pass.
+template <class R, int D, int M, bool EN>
+__device__ __forceinline__ void collide_staged_node_g(const Params<R>& p, const InletTables<R>& it,
+                                                      const StepArgs<R>& a, int n, R* col, int stride) {
+  int x, y, z;
+  node_xyz<R, D>(p, n, x, y, z);
+  Site<R, D> st;
+  st.init(p, x, y, z);
+  Ghost<R, D> gh;
+  gh.side = -1;
+  if (st.has_ghost()) ghost_velocity<R, D, M>(p, a.src, a.phi, x, y, z, gh);
+  stage_node<R, D, M, EN>(p, it, a.src, st, gh, col, stride);
+  SmemPull<R, D> pf{col, stride};
+  Moments<R, D, M, EN, true> mo;
+  moments_gen<R, D, M, EN, true>(pf, mo);
+  State<R, D, M> s;
+  s.template from_moments<EN, true>(p, mo, a.phi[n], EN ? R(0) : a.Tfix[n]);
+  const size_t N = p.N;
+  const R* __restrict__ g = a.mac + (size_t)(2 * D + M) * N;
+  Grad<R, D, M, EN> gr;
+  gr.divu = g[n];
+#pragma unroll
+  for (int b = 0; b < D; ++b) {
+    gr.dPi[b] = g[(size_t)(1 + b) * N + n];
+#pragma unroll
+    for (int k = 0; k < M; ++k) gr.dY[k][b] = EN ? g[(size_t)(1 + D + k * D + b) * N + n] : R(0);
+  }
+  collide_gen<R, D, M, EN>(p, pf, n, mo, s, gr, a.dst, a.status);
+}
+
+template <class R, int D, int M, bool EN, int TB>
+__global__ void __launch_bounds__(TB) k_collide_staged_g(Params<R> p, InletTables<R> it, StepArgs<R> a) {
+  extern __shared__ unsigned char smem_raw[];
+  const int n = blockIdx.x * TB + threadIdx.x;
+  if (n >= p.N) return;
+  collide_staged_node_g<R, D, M, EN>(p, it, a, n, reinterpret_cast<R*>(smem_raw) + threadIdx.x, TB);
+}
+
 // Macro-field pass from staged populations.
 template <class R, int D, int M, bool EN, int TB>
 __global__ void __launch_bounds__(TB) k_macro_staged(Params<R> p, InletTables<R> it, StepArgs<R> a) {

@@ -4,7 +4,8 @@ times, against the FP64 oracle run on the host cores.
 * 512 x 512 slab, FP32, the autotuned kernel form: 200 steps.
 * 64-capillary sweep (0.30 M nodes), FP64 batch, CUDA-graph replay: 100
   steps, every case to 1e-12.
-* 256 x 128 x 128 anode, six species, FP32, staged form: 3 steps.
+* 256 x 128 x 128 anode, six species, FP32, the default form (staged with a
+  gradient pass): 3 steps.
 * the same anode with the surface mechanism, FP32: 1 step.
 
 The oracle needs about 20 GB of host memory for the anode and a few minutes
@@ -110,17 +111,18 @@ def test_batch_64_capillaries_fp64(L):
     assert worst_ratio < 1.0, worst
 
 
-def test_anode_full_size_fp32_staged(L):
+def test_anode_full_size_fp32_default_form(L):
+    """The form bench.py times: the staged form with a gradient pass."""
     wl = W.anode3d(steps=3)
     g = L.Lattice(wl, precision=L.LBM_FP32)
-    g.set_variant(3)
+    assert g.variant() == 5
     g.step(wl.steps)
     g.sync()
     o = oracle.Oracle(wl)
     o.step(wl.steps)
     e = rel(g.moments(L.LBM_MOM_RHO_A), o.moments(oracle.MOM_RHO_A))
     ef = flux_err(L, g, o, wl)
-    print("anode 256x128x128 FP32, 3 steps: densities %.2e, fluxes %.2e" % (e, ef))
+    print("anode 256x128x128 FP32 (gradient-pass form), 3 steps: densities %.2e, fluxes %.2e" % (e, ef))
     assert e < 1e-5 and ef < 1e-5
 
 

@@ -1,8 +1,11 @@
 """Run one kernel form for a few steps on a small case (for profilers).
 
-    python -m paper_2409_02930_gb300.run_form anode|react|batch|adjoint
+    python -m paper_2409_02930_gb300.run_form anode|anode_gather|react|batch|adjoint
 
-anode:   D3Q27 anode 64x32x32, six species, FP32, staged form (variant 3), 3 steps
+anode:   D3Q27 anode 64x32x32, six species, FP32, the default form (staged with
+         a gradient pass, variant 5), 3 steps
+anode_gather: the same with the staged form that gathers the gradient
+         inputs itself (variant 3)
 react:   the same lattice with the seeded surface mechanism, FP32, 3 steps
 batch:   the 64-capillary sweep, FP32, staged persistent form (variant 7), 5 steps
          launched one by one (timing on, so no graph replay)
@@ -17,9 +20,9 @@ from . import workloads as W
 
 
 def main(which: str) -> None:
-    if which == "anode":
+    if which in ("anode", "anode_gather"):
         g = lbm.Lattice(W.anode3d(nx=64, ny=32, nz=32, steps=3), precision=lbm.LBM_FP32)
-        g.set_variant(3)
+        g.set_variant(5 if which == "anode" else 3)
         g.step(3)
         g.sync()
     elif which == "react":

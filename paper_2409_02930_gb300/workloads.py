@@ -170,6 +170,17 @@ def _he_ar():
     return m, D, mu, cv
 
 
+def _he_ne_ar():
+    """He, Ne, Ar-like masses with synthetic binary diffusivities at 300 K, 1 atm."""
+    m = np.array([4.0e-3, 20.0e-3, 40.0e-3])
+    D = np.array([[0.0, 1.1e-4, 7.0e-5],
+                  [1.1e-4, 0.0, 3.2e-5],
+                  [7.0e-5, 3.2e-5, 0.0]])
+    mu = np.array([1.99e-5, 3.2e-5, 2.27e-5])
+    cv = np.array([1.5, 1.5, 1.5])
+    return m, D, mu, cv
+
+
 def _h2_h2o_n2():
     m = np.array([2.0e-3, 18.0e-3, 28.0e-3])
     D = np.array([[0.0, 8.0e-4, 7.5e-4],
@@ -258,6 +269,42 @@ def adjoint_slab(nx=256, ny=256, steps=1000, name=None, face_ramp=8) -> Workload
     w = np.minimum(1.0, np.minimum(xs, nx - 1 - xs) / float(face_ramp))
     wl.X_init = (1 - w)[None, :] * lin + w[None, :] * wl.X_init
     return wl
+
+
+def ternary_capillary(P, nx=480, ny=4, T=300.0, pore_radius=1.0e-6, steps=200000,
+                      X_lo=(0.8, 0.15, 0.05), X_hi=(0.05, 0.25, 0.7), name=None,
+                      dx_per_radius=1.0) -> Workload:
+    """Ternary counter-diffusion of He, Ne, Ar-like gases (4, 20, 40 g/mol) in
+    an open capillary between two reservoirs of fixed composition at
+    pressure P, isothermal; the mole fractions start linear between the two
+    reservoir compositions.  Node spacing as in capillary_batch (at most
+    the pore radius, and small enough for omega <= 1.4)."""
+    m, D, mu, cv = _he_ne_ar()
+    theta = 1.0 / 3.0
+    dt_per_dx = np.sqrt(theta * m.min() / (R_UNIV * T))
+    dx = min(dx_per_radius * pore_radius, mu.min() / (P * (1.0 / 1.4 - 0.5) * dt_per_dx))
+    N = nx * ny
+    xs = np.tile(np.arange(nx), ny)
+    s = xs / (nx - 1.0)
+    X_lo = np.asarray(X_lo, float)
+    X_hi = np.asarray(X_hi, float)
+    X = X_lo[:, None] * (1.0 - s) + X_hi[:, None] * s
+    return Workload(
+        name=name or f"ternary_capillary_{nx}x{ny}_{P:.0f}Pa", nx=nx, ny=ny, nz=1,
+        bc_lo=BC_INLET, bc_hi=BC_INLET, M=3, energy=False, knudsen=True,
+        dx=dx, theta_max=theta, T_scale=T, T_ref=300.0, P_ref=ATM,
+        molar_mass=m, D_ref=D, mu_ref=mu, mu_exp=0.7, Pr=0.7, bulk_ratio=1.0,
+        cv_factor=cv, U0=np.zeros(3), T_thermo=0.0, tortuosity=1.0,
+        pore_radius=pore_radius, porosity=np.ones(N), X_init=X,
+        T_init=np.full(N, T), P_init=np.full(N, P),
+        X_in_lo=X_lo, X_in_hi=X_hi, T_in_lo=T, T_in_hi=T, P_in_lo=P, P_in_hi=P,
+        steps=steps)
+
+
+def ternary_sweep(nx=480, ny=4, n_pressures=5, P_lo=60.0, P_hi=40422.0) -> List[Workload]:
+    """The ternary capillary at pressures log-spaced from 60 Pa to 40,422 Pa
+    (the pressure range of the capillary experiment of Sec. 5.1)."""
+    return [ternary_capillary(float(P), nx=nx, ny=ny) for P in np.geomspace(P_lo, P_hi, n_pressures)]
 
 
 def capillary_batch(n_cases=64, seed=5, ny=4, steps=2000, nmin=128, nmax=4096) -> List[Workload]:

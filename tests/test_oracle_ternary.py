@@ -1,0 +1,79 @@
+"""Pins of the oracle's steady dusty-gas boundary-value solver (Sec. 5.1,
+eq:constit2), the reference for the ternary capillary sweep: it must reduce
+to the integrated binary closed form when a species is absent, to pure
+Knudsen diffusion when the binary diffusivities are large, obey Graham's
+law between equal pressures, and carry the profile exactly from one end to
+the other."""
+import numpy as np
+import pytest
+from scipy.integrate import solve_ivp
+
+from oracle import dgm_bvp as B
+from paper_2409_02930_gb300 import workloads as W
+
+T = 300.0
+M_HE_NE_AR = np.array([4.0e-3, 20.0e-3, 40.0e-3])
+
+
+def setup(P):
+    D = W._he_ne_ar()[1] * (W.ATM / P)           # binary diffusivities at P
+    Dk = B.knudsen_diffusivity(1.0e-6, T, M_HE_NE_AR)
+    c = P / (B.R_U * T)
+    return D, Dk, c
+
+
+@pytest.mark.parametrize("P", [60.0, 1557.0, 40422.0])
+def test_reduces_to_binary_closed_form(P):
+    D, Dk, c = setup(P)
+    L = 48e-6
+    N = B.fluxes([0.9, 0.1, 0.0], [0.2, 0.8, 0.0], L, D, Dk, c)
+    ref = B.binary_closed_form(0.9, 0.2, L, D[0, 1], Dk[0], M_HE_NE_AR[0], M_HE_NE_AR[1], c)
+    assert abs(N[0] / ref - 1.0) < 1e-10
+    assert abs(N[1] / N[0] + np.sqrt(M_HE_NE_AR[0] / M_HE_NE_AR[1])) < 1e-10     # Graham
+    assert abs(N[2]) < 1e-12 * abs(N[0])
+
+
+def test_knudsen_limit():
+    D, Dk, c = setup(1557.0)
+    X0, XL, L = np.array([0.8, 0.15, 0.05]), np.array([0.05, 0.25, 0.7]), 48e-6
+    N = B.fluxes(X0, XL, L, D * 1e12, Dk, c)
+    np.testing.assert_allclose(N, c * Dk * (X0 - XL) / L, rtol=1e-9)
+
+
+@pytest.mark.parametrize("P", [305.0, 7937.0])
+def test_ternary_graham_and_profile(P):
+    """Between equal end pressures sum_a N_a/D^k_a = 0; integrating the ODE
+    with the solved fluxes by a general-purpose integrator reaches the far
+    end composition."""
+    D, Dk, c = setup(P)
+    X0, XL, L = np.array([0.8, 0.15, 0.05]), np.array([0.05, 0.25, 0.7]), 48e-6
+    N = B.fluxes(X0, XL, L, D, Dk, c)
+    assert abs(np.sum(N / Dk)) < 1e-10 * np.max(np.abs(N / Dk))
+
+    def rhs(x, X):
+        out = np.empty(3)
+        for a in range(3):
+            s = N[a] / Dk[a]
+            for b in range(3):
+                if b != a:
+                    s += (X[b] * N[a] - X[a] * N[b]) / D[a, b]
+            out[a] = -s / c
+        return out
+
+    sol = solve_ivp(rhs, (0.0, L), X0, rtol=1e-11, atol=1e-13)
+    np.testing.assert_allclose(sol.y[:, -1], XL, atol=1e-8)
+
+
+def test_partial_pressure_form_matches_isobaric_form():
+    """With equal end pressures the pressure-gradient form gives the
+    isobaric fluxes; a higher pressure at x = 0 adds flow down the gradient
+    for every species."""
+    P = 1557.0
+    D, Dk, c = setup(P)
+    X0, XL, L = np.array([0.8, 0.15, 0.05]), np.array([0.05, 0.25, 0.7]), 48e-6
+    N_iso = B.fluxes(X0, XL, L, D, Dk, c)
+    D0 = W._he_ne_ar()[1] * W.ATM
+    N_p = B.fluxes_partial(X0 * P, XL * P, L, D0, Dk, T)
+    np.testing.assert_allclose(N_p, N_iso, rtol=1e-9)
+    N_up = B.fluxes_partial(X0 * P * 1.01, XL * P, L, D0, Dk, T)
+    assert np.all(N_up > N_p)

@@ -13,7 +13,8 @@ def declared_functions():
     names = []
     for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
         if fn.endswith(".h"):
-            src = open(os.path.join(ROOT, "include", fn)).read()
+            with open(os.path.join(ROOT, "include", fn)) as f:
+                src = f.read()
             src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
             names += re.findall(r"^\s*(?:[A-Za-z_][\w\s\*]*?[\s\*])(lbm_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))

@@ -21,7 +21,8 @@ def test_algorithmic_bytes_per_node():
 
 def test_traffic_table_entries_parse():
     path = os.path.join(ROOT, "profiles", "traffic_per_launch.txt")
-    keys = [line.split()[0] for line in open(path) if line.strip() and not line.startswith("#")]
+    with open(path) as f:
+        keys = [line.split()[0] for line in f if line.strip() and not line.startswith("#")]
     assert "slab512x512_fp32_variant8" in keys
     for k in keys:
         t = bench.profiled_traffic(k)

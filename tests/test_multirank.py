@@ -39,7 +39,7 @@ def _rank_main(rank, ws, port, out):
 def test_two_gloo_ranks_take_the_slowest_time():
     ws = 2
     port = _free_port()
-    mgr = mp.Manager()
+    mgr = mp.get_context("spawn").Manager()      # no fork of a multi-threaded parent
     out = mgr.dict()
     mp.spawn(_rank_main, args=(ws, port, out), nprocs=ws, join=True)
     assert out[0][0] == out[1][0] == 20.0

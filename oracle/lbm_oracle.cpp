@@ -497,13 +497,19 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   for (int a = 0; a < M; ++a)
     for (int al = 0; al < 3; ++al)
       ua[a][al] = (m.rho_a[a] < 1e-14 * m.rho_s) ? m.u[al] : m.j_a[a][al] / m.rho_a[a];   // R11
+  // eqn:transform1 with the Knudsen part taken on the component velocity
+  // (reading R27): the trapezoidal rule of Sec. 2.3 applied to the Knudsen
+  // relaxation (f*_a - f^k_a)/tau^k_a, whose f^k rests (eq:fKnudsen), acts on
+  // u + V_a, not on V_a alone, which adds -(dt/2tau^k_a) u to the printed
+  // right-hand side (the printed system is the u = 0 case).
   real A[MMAX * MMAX], rhs[MMAX * 3], V[MMAX * 3];
   for (int a = 0; a < M; ++a) {
     for (int b = 0; b < M; ++b) {
       if (a == b) A[a * M + b] = 1.0 + 0.5 * inv_tau[a] + 0.5 * inv_tauk[a];   // eqn:transform1
       else A[a * M + b] = -0.5 * m.Y[b] / tau_ab[a][b];
     }
-    for (int al = 0; al < 3; ++al) rhs[a * 3 + al] = (al < D) ? (ua[a][al] - m.u[al]) : 0.0;
+    for (int al = 0; al < 3; ++al)
+      rhs[a * 3 + al] = (al < D) ? (ua[a][al] - m.u[al] - 0.5 * inv_tauk[a] * m.u[al]) : 0.0;
   }
   householder_qr_solve(M, A, 3, rhs, V);
   // condition bound (reading R12): ||A||_inf * ||A^-1||_inf <= max row sum / min(1 + dt/2tau^k)
@@ -559,11 +565,23 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   }
 
   // --- momentum lattice (a8): eqn:f / eqn:f_source ---------------------------
-  // net Knudsen force eqn:netKnudsenForce with P X_b / D^k_b = rho_b / tau^k_b and
-  // the component velocity u_b = u + V_b of the discrete system (reading R8).
+  // net Knudsen force eqn:netKnudsenForce with P X_b / D^k_b = rho_b / tau^k_b
+  // and the component velocity u_b = u* + (V_b - Vbar) (reading R8): the
+  // mixture velocity plus the diffusion velocity taken relative to the
+  // species' mass average Vbar = sum_c Y_c V_c, whose mass-weighted sum
+  // vanishes as eq:totmomSpec requires.  The mixture velocity u* is the
+  // momentum lattice's, at the middle of the step (u* = u + dt F^k/(2 rho)):
+  // the trapezoidal rule of Sec. 2.3 applied to the drag of the mixture, so
+  //   F^k = -sum_b rho_b (u + V_b - Vbar)/tau^k_b / (1 + (dt/2) sum_b (rho_b/rho)/tau^k_b).
   real Fk[3] = {0, 0, 0};
-  for (int b = 0; b < M; ++b)
-    for (int al = 0; al < D; ++al) Fk[al] -= m.rho_a[b] * (m.u[al] + V[b * 3 + al]) * inv_tauk[b];
+  real kdrag = 0.0;
+  for (int b = 0; b < M; ++b) kdrag += (m.rho_a[b] / m.rho_f) * inv_tauk[b];
+  for (int al = 0; al < D; ++al) {
+    real Vbar = 0.0;
+    for (int c = 0; c < M; ++c) Vbar += m.Y[c] * V[c * 3 + al];
+    for (int b = 0; b < M; ++b) Fk[al] -= m.rho_a[b] * (m.u[al] + V[b * 3 + al] - Vbar) * inv_tauk[b];
+    Fk[al] /= 1.0 + 0.5 * kdrag;
+  }
   for (int al = 0; al < 3; ++al) const_cast<Oracle&>(o).dg_Fk[(size_t)al * o.N + n] = Fk[al];
   // viscosity (reading R13): mu = sum_a X_a mu_a(T), mu_a = mu_ref,a (T/Tref)^mu_exp
   real mu = 0.0;

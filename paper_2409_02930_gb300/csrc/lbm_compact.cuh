@@ -283,11 +283,22 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
   R FX[D][3];
   {
     const R irf = R(1) / (phi * s.rho_f);
+    R kdrag = R(0);
+#pragma unroll
+    for (int a = 0; a < M; ++a) kdrag += s.rho_a[a] * tr.inv_tauk[a];
+    const R inv_drag = R(1) / (R(1) + R(0.5) * kdrag / s.rho_f);
 #pragma unroll
     for (int b = 0; b < D; ++b) {
+      // component velocity u* + (V_a - Vbar): diffusion velocities taken
+      // relative to the species' mass average, the mixture velocity at the
+      // middle of the step (trapezoidal drag of the mixture; reading R8)
+      R Vbar = R(0);
+#pragma unroll
+      for (int a = 0; a < M; ++a) Vbar += s.Y[a] * tr.V[a][b];
       R Fk = R(0);
 #pragma unroll
-      for (int a = 0; a < M; ++a) Fk -= s.rho_a[a] * (s.u[b] + tr.V[a][b]) * tr.inv_tauk[a];
+      for (int a = 0; a < M; ++a) Fk -= s.rho_a[a] * (s.u[b] + tr.V[a][b] - Vbar) * tr.inv_tauk[a];
+      Fk *= inv_drag;
       R uex = s.u[b] + Fk / (omega * s.rho_f);
       R Pex = s.Rg * s.T + w[b] * w[b] + bulk * gr.divu * irf + (R(2) - omega) / (R(2) * omega) * irf * gr.dPi[b];
       psi3<R>(uex * inv_phi, Pex, FX[b]);

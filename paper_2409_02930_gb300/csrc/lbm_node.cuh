@@ -289,7 +289,10 @@ struct Transport {
       beta[a] = acc / (R(2) + acc);           // dt/(2 tau + dt) with dt = 1
       inv_tauk[a] = p.knudsen ? p.knc[a] * sqrt_<R>(s.T) / s.phi : R(0);
     }
-    // A V = u_a - u, A_aa = 1 + 1/(2tau_a) + 1/(2tau^k_a), A_ab = -Y_b/(2 tau_ab)
+    // A V = u_a - u - u/(2tau^k_a), A_aa = 1 + 1/(2tau_a) + 1/(2tau^k_a),
+    // A_ab = -Y_b/(2 tau_ab): the trapezoidal rule on the Knudsen relaxation
+    // toward the resting f^k acts on the component velocity u + V_a, which
+    // adds -u/(2tau^k_a) to the right-hand side (reading R27)
     R A[M][M], B[M][D];
     R amax = R(0), dmin = R(1e30);
 #pragma unroll
@@ -313,7 +316,8 @@ struct Transport {
       bool tiny = s.rho_a[a] < R(1e-14) * s.rho_s;
       if (ScalarTraits<R>::single) tiny = tiny || !(sabs[a] <= R(1e4) * s.phi * s.rho_a[a]);
 #pragma unroll
-      for (int b = 0; b < D; ++b) B[a][b] = tiny ? R(0) : (ja[a * D + b] / s.rho_a[a] - s.u[b]);
+      for (int b = 0; b < D; ++b)
+        B[a][b] = (tiny ? R(0) : (ja[a * D + b] / s.rho_a[a] - s.u[b])) - R(0.5) * inv_tauk[a] * s.u[b];
     }
     used_fp64 = 0;
     if (sizeof(R) == 4 && amax > p.kappa_thr * dmin) {

@@ -114,3 +114,53 @@ def test_pore_radius_and_tortuosity_enter_as_a_ratio(jvps):
     # d/d ln r_p = - d/d ln tau
     assert abs(g[6] + g[7]) <= 1e-12 * max(abs(g[6]), abs(J)), (g[6], g[7])
     assert abs(g[6]) > 1e-8 * abs(J)        # the Knudsen term matters here
+
+
+def test_full_gradient_on_a_4x4x4_lattice_by_brute_force():
+    """Brute force on a 4^3 D3Q27 lattice (three species, energy, Knudsen,
+    reservoirs at both x faces): the gradient of the outlet flux with respect
+    to all 64 porosities, from the dual build one node per lane, against
+    central differences of the plain build node by node."""
+    base = W.slab(nx=4, ny=4, steps=12, bc_x=W.BC_INLET, X_lo=[0.7, 0.2, 0.1], X_hi=[0.1, 0.3, 0.6],
+                  name="brute_4x4x4")
+
+    def make(phi=None):
+        wl = W.slab(nx=4, ny=4, steps=12, bc_x=W.BC_INLET, X_lo=[0.7, 0.2, 0.1], X_hi=[0.1, 0.3, 0.6],
+                    name="brute_4x4x4")
+        wl.nz = 4
+        wl.porosity = W.porosity_field((4, 4, 4), 2.0, 41) if phi is None else phi
+        wl.X_init = W.random_mole_fractions(3, 64, 42)
+        wl.T_init = np.full(64, base.T_init[0])
+        wl.P_init = np.full(64, base.P_init[0])
+        return wl
+
+    def J3(o, wl, lane=None):
+        j = o.moments(oracle.MOM_J_A, lane=lane).reshape(wl.M, 3, 4, 4, 4)
+        return float(j[0, 0, :, :, wl.nx - 2].sum())
+
+    wl = make()
+    grad = np.zeros(64)
+    for start in range(0, 64, oracle.LANES):
+        o = oracle.Oracle(wl, dual=True)
+        dphi = np.zeros((oracle.LANES, 64))
+        for k in range(oracle.LANES):
+            dphi[k, start + k] = 1.0
+        o.set_tangents(dphi=dphi)
+        o.step(wl.steps)
+        for k in range(oracle.LANES):
+            grad[start + k] = J3(o, wl, lane=k)
+    eps = 1e-6
+    fd = np.zeros(64)
+    for n in range(64):
+        vals = []
+        for s in (1.0, -1.0):
+            phi = wl.porosity.copy()
+            phi[n] += s * eps
+            w = make(phi)
+            p = oracle.Oracle(w)
+            p.step(w.steps)
+            vals.append(J3(p, w))
+        fd[n] = (vals[0] - vals[1]) / (2 * eps)
+    scale = np.abs(grad).max()
+    assert scale > 0
+    np.testing.assert_allclose(fd, grad, rtol=0, atol=1e-6 * scale)

@@ -484,3 +484,75 @@ def test_d3q27_isotropy():
     np.testing.assert_allclose(ub[0], ua[0], rtol=0, atol=1e-12 * sc)
     np.testing.assert_allclose(ub[2], ua[1], rtol=0, atol=1e-12 * sc)
     assert np.abs(ua[2]).max() < 1e-12 * sc and np.abs(ub[1]).max() < 1e-12 * sc
+
+
+# ---------------------------------------------------------------------------
+# bounce-back faces (the electrode / electrolyte interface of Sec. 5.2)
+# ---------------------------------------------------------------------------
+def _closed_box(nx=12, ny=8, U=None, knudsen=True, energy=True, seed=31):
+    wl = W.slab(nx=nx, ny=ny, seed_phi=seed, seed_X=seed + 1, energy=energy, name="closed_box")
+    wl.bc_lo = wl.bc_hi = W.BC_BOUNCEBACK
+    wl.knudsen = knudsen
+    wl.U_init = U
+    return wl
+
+
+def test_bounceback_box_conserves_every_species():
+    """Bounce-back at both x faces closes the box: no mass crosses a wall, so
+    every species' total sum_i f_ai over the box stays constant (to rounding),
+    and so do the momentum lattice's mass and the energy lattice's total."""
+    wl = _closed_box()
+    o = oracle.Oracle(wl)
+    p0 = o.pops()
+    tot0 = p0.sum(axis=(1, 2))
+    o.step(200)
+    tot1 = o.pops().sum(axis=(1, 2))
+    np.testing.assert_allclose(tot1, tot0, rtol=1e-13, atol=0)
+
+
+def _mirror(a, nx, ny):
+    return a.reshape(a.shape[:-1] + (ny, nx))[..., ::-1].reshape(a.shape)
+
+
+def test_bounceback_box_keeps_mirror_symmetry():
+    """A field symmetric under x -> nx-1-x stays symmetric between two
+    bounce-back walls: densities and temperature mirror, u_x changes sign."""
+    nx, ny = 12, 8
+    wl = _closed_box(nx, ny)
+    wl.porosity = 0.5 * (wl.porosity + _mirror(wl.porosity, nx, ny))
+    wl.X_init = 0.5 * (wl.X_init + _mirror(wl.X_init, nx, ny))
+    o = oracle.Oracle(wl)
+    o.step(150)
+    r = o.moments(oracle.MOM_RHO_A)
+    np.testing.assert_allclose(_mirror(r, nx, ny), r, rtol=1e-12)
+    T = o.moments(oracle.MOM_T)
+    np.testing.assert_allclose(_mirror(T, nx, ny), T, rtol=1e-12)
+    u = o.moments(oracle.MOM_U)
+    sc = np.abs(u).max()
+    assert sc > 0
+    np.testing.assert_allclose(_mirror(u[0], nx, ny), -u[0], rtol=0, atol=1e-11 * sc)
+    np.testing.assert_allclose(_mirror(u[1], nx, ny), u[1], rtol=0, atol=1e-11 * sc)
+
+
+def test_bounceback_walls_do_not_slip():
+    """Bounce-back reverses the whole velocity at the wall (no slip): a
+    uniform flow along the walls loses momentum to them, decaying every step,
+    while the momentum across them stays zero.  (A specular rule would keep
+    the tangential momentum; without Knudsen drag nothing else removes it.)"""
+    nx, ny = 12, 4
+    U = np.zeros((2, nx * ny))
+    U[1] = 10.0                                           # m/s along the walls
+    wl = _closed_box(nx, ny, U=U, knudsen=False, energy=False)
+    wl.porosity[:] = 0.5
+    wl.X_init[:] = np.array([[0.3], [0.3], [0.4]])
+    o = oracle.Oracle(wl)
+    c, _ = _lattice(2)
+    jy = []
+    for _ in range(6):
+        o.step(20)
+        f = o.pops()[wl.M]
+        jy.append(np.einsum("in,i->", f, c[:, 1]))
+        jx = np.einsum("in,i->", f, c[:, 0])
+        assert abs(jx) < 1e-12 * abs(jy[-1])
+    assert all(b < a for a, b in zip(jy, jy[1:]))
+    assert jy[-1] < 0.9 * jy[0]

@@ -93,3 +93,120 @@ def test_unified_internal_energy_is_conserved():
     scale = np.abs(pre[M + 1].sum(0)).max() * o.cvel ** 2
     assert np.abs(dads).max() > 1e-9 * scale                          # the exchange is not trivial
     assert np.max(np.abs(dg + dads)) < 1e-7 * scale
+
+
+# ---------------------------------------------------------------------------
+# closed forms of the backward-Euler extents (reading R16) for mechanisms
+# small enough to solve by hand: these fix the reactant orders, the
+# Arrhenius constant k = A exp(-Ea/(R_U T)) with Ea in J/mol, the gas-side
+# scale a^(s)/phi of eq:totalFluidReactionRate and backward (not forward)
+# Euler
+# ---------------------------------------------------------------------------
+T_RX, PHI_RX, A_S, GAMMA = 1000.0, 0.5, 1.0e7, 2.6e-5
+M_A, M_B = 28.0e-3, 40.0e-3
+
+
+def _uniform_reactive(nu_gas, nu_surf, A, Ea, Xs0, X_gas=(0.5, 0.5), nx=3, ny=3):
+    """Uniform periodic 2-D lattice of gas A and an inert gas B at 1 atm and
+    1000 K (isothermal) over a surface with the given steps; every node is
+    the same well-mixed reactor."""
+    N = nx * ny
+    S = len(Xs0)
+    R = len(A)
+    mech = W.Mechanism(S=S, R=R, nu_gas=np.asarray(nu_gas, float), nu_surf=np.asarray(nu_surf, float),
+                       A=np.asarray(A, float), Ea=np.asarray(Ea, float), gamma=GAMMA, a_s=A_S,
+                       surf_molar_mass=np.full(S, M_A), surf_cv_factor=np.zeros(S), surf_U0=np.zeros(S),
+                       gas_U0_molar=np.zeros(2), elements_gas=np.eye(2, dtype=int),
+                       elements_surf=np.zeros((S, 2), dtype=int), Xs_init=np.asarray(Xs0, float))
+    wl = W.Workload(
+        name="uniform_reactor", nx=nx, ny=ny, nz=1, bc_lo=W.BC_PERIODIC, bc_hi=W.BC_PERIODIC, M=2,
+        energy=False, knudsen=False, dx=1.0e-6, theta_max=1.0 / 3.0, T_scale=T_RX, T_ref=T_RX, P_ref=W.ATM,
+        molar_mass=np.array([M_A, M_B]), D_ref=np.array([[0.0, 2e-4], [2e-4, 0.0]]),
+        mu_ref=np.array([4e-5, 4e-5]), mu_exp=0.7, Pr=0.7, bulk_ratio=1.0, cv_factor=np.array([2.5, 1.5]),
+        U0=np.zeros(2), T_thermo=0.0, tortuosity=1.0, pore_radius=1e-6, porosity=np.full(N, PHI_RX),
+        X_init=np.tile(np.asarray(X_gas, float)[:, None], (1, N)), T_init=np.full(N, T_RX),
+        P_init=np.full(N, W.ATM), X_in_lo=np.asarray(X_gas, float), X_in_hi=np.asarray(X_gas, float),
+        T_in_lo=T_RX, T_in_hi=T_RX, P_in_lo=W.ATM, P_in_hi=W.ATM, steps=1, mechanism=mech)
+    return wl
+
+
+def _rate_constant_for(dt, target):
+    """Prefactor whose k at T_RX with Ea = 100 kJ/mol is target / dt."""
+    return target / dt / np.exp(-100.0e3 / (R_U * T_RX)), 100.0e3
+
+
+def test_adsorption_extent_is_the_backward_euler_root():
+    """A + s -> A(s), r = k c_A theta_s.  One backward-Euler step solves
+    xi = dt k (c0 - alpha xi)(theta0 - xi), alpha = a^(s)/phi: the smaller
+    root of dt k alpha xi^2 - (1 + dt k (c0 + alpha theta0)) xi + dt k c0 theta0 = 0.
+    The coverage of A(s) grows by xi/Gamma and the gas density of A falls by
+    a^(s) m_A xi / phi (eq:totalFluidReactionRate, eq:molarToMassRates)."""
+    probe = oracle.Oracle(_uniform_reactive([[-1, 0]], [[-1, 1]], [1.0], [0.0], [0.9, 0.1]))
+    dt = probe.dt
+    c0 = 0.5 * W.ATM / (R_U * T_RX)
+    th0 = 0.9 * GAMMA
+    alpha = A_S / PHI_RX
+    A, Ea = _rate_constant_for(dt, 1.0 / (c0 + alpha * th0))     # dt k (c0 + alpha theta0) = 1
+    wl = _uniform_reactive([[-1, 0]], [[-1, 1]], [A], [Ea], [0.9, 0.1])
+    o = oracle.Oracle(wl)
+    rho0 = o.moments(oracle.MOM_RHO_A)
+    o.step(1)
+    k = A * np.exp(-Ea / (R_U * T_RX))
+    a2, a1, a0 = dt * k * alpha, -(1.0 + dt * k * (c0 + alpha * th0)), dt * k * c0 * th0
+    xi = (-a1 - np.sqrt(a1 * a1 - 4 * a2 * a0)) / (2 * a2)
+    xi_forward = dt * k * c0 * th0
+    assert abs(xi / xi_forward - 1.0) > 0.2                    # the two schemes are far apart here
+    Xs = o.moments(oracle.MOM_XS)
+    np.testing.assert_allclose(Xs[1], 0.1 + xi / GAMMA, rtol=1e-12)
+    np.testing.assert_allclose(Xs[0], 0.9 - xi / GAMMA, rtol=1e-12)
+    rho = o.moments(oracle.MOM_RHO_A)
+    np.testing.assert_allclose(rho[0], rho0[0] - A_S * M_A * xi / PHI_RX, rtol=1e-12)
+    np.testing.assert_allclose(rho[1], rho0[1], rtol=1e-14)
+
+
+def test_dissociative_adsorption_extent_is_the_cubic_root():
+    """A + 2 s -> 2 A(s), r = k c_A theta_s^2: second order in the empty site.
+    Backward Euler: xi = dt k (c0 - alpha xi)(theta0 - 2 xi)^2, the root in
+    [0, min(c0/alpha, theta0/2)] of that cubic."""
+    probe = oracle.Oracle(_uniform_reactive([[-1, 0]], [[-2, 2]], [1.0], [0.0], [0.9, 0.1]))
+    dt = probe.dt
+    c0 = 0.5 * W.ATM / (R_U * T_RX)
+    th0 = 0.9 * GAMMA
+    alpha = A_S / PHI_RX
+    A, Ea = _rate_constant_for(dt, 1.0 / (th0 * (c0 + alpha * th0)))
+    wl = _uniform_reactive([[-1, 0]], [[-2, 2]], [A], [Ea], [0.9, 0.1])
+    o = oracle.Oracle(wl)
+    o.step(1)
+    k = A * np.exp(-Ea / (R_U * T_RX))
+    # dt k (c0 - alpha xi)(theta0 - 2 xi)^2 - xi = 0
+    p = dt * k * np.polymul([-alpha, c0], np.polymul([-2.0, th0], [-2.0, th0])) - np.array([0, 0, 1.0, 0])
+    roots = np.roots(p)
+    hi = min(c0 / alpha, th0 / 2)
+    xi = [r.real for r in roots if abs(r.imag) < 1e-12 * hi and 0 <= r.real <= hi]
+    assert len(xi) == 1
+    Xs = o.moments(oracle.MOM_XS)
+    np.testing.assert_allclose(Xs[1], 0.1 + 2 * xi[0] / GAMMA, rtol=1e-11)
+
+
+def test_reversible_adsorption_reaches_its_equilibrium():
+    """A + s -> A(s) (k_f) and A(s) -> A + s (k_b): the steady coverages
+    satisfy k_f c_A theta_s = k_b theta_A with the A inventory
+    phi c_A + a^(s) theta_A and the sites theta_s + theta_A = Gamma fixed."""
+    probe = oracle.Oracle(_uniform_reactive([[-1, 0]], [[-1, 1]], [1.0], [0.0], [0.9, 0.1]))
+    dt = probe.dt
+    c0 = 0.5 * W.ATM / (R_U * T_RX)
+    Af, Ea = _rate_constant_for(dt, 0.02 / (c0 * GAMMA) * GAMMA)   # k_f c0 dt = 0.02
+    Ab, _ = _rate_constant_for(dt, 0.05)                              # k_b dt = 0.05
+    wl = _uniform_reactive([[-1, 0], [1, 0]], [[-1, 1], [1, -1]], [Af, Ab], [Ea, Ea], [0.9, 0.1])
+    o = oracle.Oracle(wl)
+    o.step(3000)
+    kf, kb = Af * np.exp(-Ea / (R_U * T_RX)), Ab * np.exp(-Ea / (R_U * T_RX))
+    nT = PHI_RX * c0 + A_S * 0.1 * GAMMA                     # moles of A per volume of medium
+    # kf (nT - a_s thA)/phi (Gamma - thA) = kb thA
+    q = np.polymul([-A_S / PHI_RX, nT / PHI_RX], [-1.0, GAMMA]) * kf - np.array([0, kb, 0])
+    thA = [r.real for r in np.roots(q) if abs(r.imag) == 0 and 0 <= r.real <= GAMMA]
+    assert len(thA) == 1
+    Xs = o.moments(oracle.MOM_XS)
+    np.testing.assert_allclose(Xs[1], thA[0] / GAMMA, rtol=1e-10)
+    cA = o.moments(oracle.MOM_RHO_A)[0] / M_A
+    np.testing.assert_allclose(kf * cA * Xs[0] * GAMMA, kb * Xs[1] * GAMMA, rtol=1e-9)

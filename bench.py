@@ -89,18 +89,36 @@ def other_forms(stream, torch, lbm):
         "achieved_gbs": b.N * algorithmic_bytes_per_node(wls[0], 4) / (ms / 1e3) / 1e9,
         "note": "state of 2 x 32 MB stays in L2: L2-bound, not HBM"}
     b.close()
+    # error of the FP32 batch after 1000 steps against the FP64 batch (which
+    # equals the oracle case by case), worst case and species
+    b32 = lbm.Batch(wls, precision=lbm.LBM_FP32, stream=sp)
+    b64 = lbm.Batch(wls, precision=lbm.LBM_FP64, stream=sp)
+    b32.step(1000)
+    b64.step(1000)
+    errs = {}
+    for nm in ("RHO_A", "J_A"):
+        k = getattr(lbm, "LBM_MOM_" + nm)
+        errs[nm] = max(float(np.max(np.abs(x[a] - y[a])) / np.max(np.abs(y[a])))
+                       for x, y in zip(b32.moments(k), b64.moments(k)) for a in range(x.shape[0]))
+    out["batch_64_capillaries_fp32"]["error_vs_fp64_after_1000_steps"] = errs
+    b32.close()
+    b64.close()
     # adjoint form: 256 x 256 slab, checkpoints every 50
     wl = W.adjoint_slab()
     g = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
     n_adj = 100
     t0 = time.perf_counter()
-    g.adjoint(n_adj, 50)
+    _, g32, _, _ = g.adjoint(n_adj, 50)
     el = time.perf_counter() - t0
+    g.close()
+    g = lbm.Lattice(wl, precision=lbm.LBM_FP64, stream=sp)
+    _, g64, _, _ = g.adjoint(n_adj, 50)
+    g.close()
     out["adjoint_256x256_fp32"] = {
         "ms_per_step": el * 1e3 / n_adj, "steps": n_adj, "nodes": wl.N,
         "value": wl.N * wl.L * n_adj / el / 1e6, "unit": UNIT,
-        "note": "forward with checkpoints + recomputation + reverse sweep per step (wall clock)"}
-    g.close()
+        "note": "forward with checkpoints + recomputation + reverse sweep per step (wall clock)",
+        "gradient_error_vs_fp64": float(np.max(np.abs(g32 - g64)) / np.max(np.abs(g64)))}
     # 3-D anode without reactions (D3Q27, six species, energy): 200 timed
     # steps after 20 warm-up steps in the default form (staged two-pass), and
     # the plain FP64 step
@@ -123,6 +141,13 @@ def other_forms(stream, torch, lbm):
         "ms_per_step": ms, "nodes": wl.N, "value": wl.N * wl.L * 1e3 / ms / 1e6, "unit": UNIT,
         "bound": "fp64 alu"}
     g.close()
+    a32 = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
+    a64 = lbm.Lattice(wl, precision=lbm.LBM_FP64, stream=sp)
+    a32.step(20)
+    a64.step(20)
+    out["anode_256x128x128_fp32"]["error_vs_fp64_after_20_steps"] = fp32_errors(a32, a64, lbm)
+    a32.close()
+    a64.close()
     # reactive 3-D anode: surface source in mixed precision
     wl = W.anode3d_reactive(steps=5)
     g = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
@@ -132,7 +157,67 @@ def other_forms(stream, torch, lbm):
         "ms_per_step": ms, "nodes": wl.N, "value": wl.N * wl.L * 1e3 / ms / 1e6, "unit": UNIT,
         "bound": "fp64 alu (surface Newton)"}
     g.close()
+    a32 = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
+    a64 = lbm.Lattice(wl, precision=lbm.LBM_FP64, stream=sp)
+    a32.step(3)
+    a64.step(3)
+    e = fp32_errors(a32, a64, lbm)
+    x, y = a32.moments(lbm.LBM_MOM_XS), a64.moments(lbm.LBM_MOM_XS)
+    e["XS"] = float(np.max(np.abs(x - y)))
+    out["anode_256x128x128_reactive_fp32"]["error_vs_fp64_after_3_steps"] = e
+    a32.close()
+    a64.close()
+    # the FP64 capillary (binary counter-diffusion, 256 x 4, 2000 steps): the
+    # plain method in double precision, timed; its parity with the oracle
+    # over these 2000 steps (1e-12 per moment) is a -m gpu test
+    wl = W.capillary()
+    g = lbm.Lattice(wl, precision=lbm.LBM_FP64, stream=sp)
+    ms = timed(g.step, wl.steps) / wl.steps
+    g.close()
+    out["capillary_256x4_fp64_2000_steps"] = {
+        "ms_per_step": ms, "nodes": wl.N, "steps": wl.steps, "value": wl.N * wl.L * 1e3 / ms / 1e6, "unit": UNIT,
+        "note": "1024 nodes: launch-bound; parity with the oracle in tests/test_gpu_parity.py"}
     return out
+
+
+def large_lattice_line(stream, torch, lbm, nx=2048, ny=2048, steps=50, warmup=5):
+    """The slab statistics on a lattice whose state (2 x 755 MB in FP32) is
+    twelve times the L2: steps back to back with no flush, so every step
+    reads its populations from HBM and its write-back lands inside the timed
+    window.  Kernel time per launch from the library's own events on its
+    stream, roofline against the algorithmic bytes."""
+    import ctypes
+    sp = ctypes.c_void_p(stream.cuda_stream)
+    wl = W.slab(nx=nx, ny=ny, steps=steps, name=f"slab_{nx}x{ny}")
+    g = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
+    variant = g.autotune(3)
+    g.set_variant(variant)
+    g.step(warmup)
+    lib = lbm.load()
+    torch.cuda.synchronize()
+    lib.lbm_set_timing(g._h, 1)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    total_ms = e0.elapsed_time(e1)
+    ms = np.zeros(3)
+    cnt = np.zeros(3, dtype=np.int64)
+    lib.lbm_get_timing(g._h, ms.ctypes.data_as(lbm._dp), cnt.ctypes.data_as(ctypes.POINTER(ctypes.c_longlong)))
+    lib.lbm_set_timing(g._h, 0)
+    g.close()
+    per_launch = ms[1] / max(cnt[1], 1)
+    alg = algorithmic_bytes_per_node(wl, 4) * wl.N
+    peak, kind = peaks()
+    return {"workload": wl.name + "_M3_energy_knudsen_fp32", "nodes": wl.N, "steps": steps, "variant": variant,
+            "ms_per_step": total_ms / steps, "value": wl.N * wl.L * steps / (total_ms / 1e3) / 1e6, "unit": UNIT,
+            "l2": "state 1.5 GB, steps back to back, no flush",
+            "roofline": {"bound": "hbm", "achieved": alg / (per_launch / 1e3) / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / (per_launch / 1e3) / 1e9 / peak, "peak_source": kind,
+                         "kernel_ms": per_launch, "algorithmic_bytes_per_launch": alg,
+                         "traffic": profiled_traffic(f"slab{nx}x{ny}_fp32_variant{variant}")}}
 
 
 def peaks():
@@ -339,19 +424,20 @@ def run_ours(args, ws, rank, local):
         t64 = sum(a.elapsed_time(b) for a, b in ev) / n64
         extra["fp64_step"] = {"ms_per_step": t64, "value": N * L / (t64 / 1e3) / 1e6, "unit": UNIT,
                               "bound": "fp64 alu"}
-        # FP32 vs FP64 GPU over the workload's whole run (5000 steps for the slab)
-        # from the same state; the FP64 GPU step equals the FP64 oracle to 1e-12
-        nerr = wl.steps
+        # FP32 against the FP64 GPU step (which equals the FP64 oracle to 1e-12)
+        # on the same state after 1000 steps (the benchmark spec's tolerance point)
+        # and after the workload's whole run (5000 steps, reported)
         a32 = lbm.Lattice(wl, precision=lbm.LBM_FP32)
         a64 = lbm.Lattice(wl, precision=lbm.LBM_FP64)
-        a32.step(nerr)
-        a64.step(nerr)
-        errs = {}
-        for nm in ("RHO_A", "J_A", "T"):
-            k = getattr(lbm, "LBM_MOM_" + nm)
-            x, y = a32.moments(k), a64.moments(k)
-            errs[nm] = float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
-        extra["fp32_vs_fp64_after_%d_steps" % nerr] = errs
+        done = 0
+        report = {}
+        for upto in (1000, 5000):
+            a32.step(upto - done)
+            a64.step(upto - done)
+            done = upto
+            report[f"after_{upto}_steps"] = fp32_errors(a32, a64, lbm)
+        extra["fp32_error_vs_fp64"] = dict(report, metric="max |a - b| / max |b| per species field (densities "
+                                           "rho_a, fluxes j_a); T field-relative", bound=1e-5)
         g64.close(); a32.close(); a64.close()
 
     out = None
@@ -380,11 +466,30 @@ def run_ours(args, ws, rank, local):
         }
         out.update(extra)
         if ws == 1 and not args.no_forms:
+            clk_forms = Clocks(local)
+            clk_forms.start()
+            time.sleep(0.3)
+            out["large_lattice"] = large_lattice_line(stream, torch, lbm)
             out["forms"] = other_forms(stream, torch, lbm)
+            out["forms"]["clocks"] = clk_forms.stop()
         if ws == 1 and not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(W.slab(nx=128, ny=128, steps=1, name="slab_128x128_sample"),
                                                seconds=args.cpu_seconds)
     g.close()
+    return out
+
+
+def fp32_errors(a32, a64, lbm):
+    """Field-relative errors of the FP32 state against the FP64 one, the worst
+    species for densities and fluxes."""
+    out = {}
+    for nm in ("RHO_A", "J_A", "T"):
+        k = getattr(lbm, "LBM_MOM_" + nm)
+        x, y = a32.moments(k), a64.moments(k)
+        if nm == "T":
+            out[nm] = float(np.max(np.abs(x - y)) / np.max(np.abs(y)))
+        else:
+            out[nm] = max(float(np.max(np.abs(x[a] - y[a])) / np.max(np.abs(y[a]))) for a in range(x.shape[0]))
     return out
 
 

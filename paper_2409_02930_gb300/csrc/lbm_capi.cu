@@ -682,6 +682,34 @@ static int step_once(lbm_ctx* x) {
   return LBM_OK;
 }
 
+// Single lattice without a surface mechanism: kGraphSteps steps from buffer
+// `cur` captured on the private capture stream into one graph (small lattices
+// are bound by the launch rate; the replay removes the per-launch host cost).
+static cudaError_t single_capture(lbm_ctx* x, int cur) {
+  cudaError_t e = cudaSuccess;
+  if (!x->cap_stream) e = cudaStreamCreateWithFlags(&x->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return e;
+  cudaStream_t keep = x->stream;
+  const int cur0 = x->cur;
+  x->stream = x->cap_stream;
+  x->cur = cur;
+  cudaGraph_t g = nullptr;
+  e = cudaStreamBeginCapture(x->cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    int rc = LBM_OK;
+    for (int s = 0; s < kGraphSteps && rc == LBM_OK; ++s) rc = step_once(x);
+    cudaError_t e2 = cudaStreamEndCapture(x->cap_stream, &g);
+    e = (rc != LBM_OK) ? cudaErrorInvalidValue : e2;
+  }
+  x->stream = keep;
+  x->cur = cur0;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&x->gexec[cur], g, 0);
+  if (g) cudaGraphDestroy(g);
+  if (e != cudaSuccess) x->gexec[cur] = nullptr;
+  x->gvariant[cur] = x->variant;
+  return e;
+}
+
 extern "C" {
 
 int lbm_step(lbm_ctx* x, int n_steps) {
@@ -692,6 +720,28 @@ int lbm_step(lbm_ctx* x, int n_steps) {
     if (rc) return rc;
     x->steps_done += n_steps;
     n_steps = 0;
+  }
+  if (x->S == 0 && !x->timing && n_steps > kGraphSteps) {
+    // one plain step first (it configures the kernels), then whole graphs of
+    // kGraphSteps steps (an even count: a replay ends on the buffer it began on)
+    int rc = step_once(x);
+    if (rc) return rc;
+    ++x->steps_done;
+    --n_steps;
+    while (n_steps >= kGraphSteps) {
+      if (!x->gexec[x->cur] || x->gvariant[x->cur] != x->variant) {
+        if (x->gexec[x->cur]) {
+          cudaGraphExecDestroy(x->gexec[x->cur]);
+          x->gexec[x->cur] = nullptr;
+        }
+        cudaError_t e = single_capture(x, x->cur);
+        if (e != cudaSuccess) return cuda_fail(x, e, "graph capture");
+      }
+      cudaError_t e = cudaGraphLaunch(x->gexec[x->cur], x->stream);
+      if (e != cudaSuccess) return cuda_fail(x, e, "graph launch");
+      n_steps -= kGraphSteps;
+      x->steps_done += kGraphSteps;
+    }
   }
   for (int s = 0; s < n_steps; ++s) {
     int rc = step_once(x);

@@ -235,8 +235,24 @@ int lbm_load(lbm_ctx* ctx, const void* buf, size_t bytes);
  */
 int lbm_step_host(lbm_ctx* ctx, const void* in_host, void* out_host, int n_steps);
 
-/* lbm_sync -- wait for the context's stream; returns the device status. */
+/* lbm_sync -- wait for the context's stream; returns the device status:
+ * LBM_ERR_NUMERIC once a step met a non-finite or non-positive density or
+ * temperature, LBM_ERR_TIMEOUT once a bounded device wait gave up (the status
+ * is kept until the context is destroyed). */
 int lbm_sync(lbm_ctx* ctx);
+
+/*
+ * lbm_set_wait_limit -- the bound of the device waits of the kernel forms
+ * that stage lattice rows with bulk tensor copies: the number of mbarrier
+ * probes a wait makes before it gives up (default 4194304).  The paper has
+ * no counterpart; the setting exists to exercise the timeout path.  A wait
+ * that gives up records LBM_ERR_TIMEOUT in the status word, the block stops
+ * stepping and first drains the copies it has in flight (those waits keep
+ * their own fixed bound), so no block ends with a copy outstanding; the
+ * step's output is then not a valid state.  With a limit of 0 every staged
+ * row wait gives up at once.  Errors: LBM_ERR_ARG (probes < 0).
+ */
+int lbm_set_wait_limit(lbm_ctx* ctx, int probes);
 
 /* lbm_info -- dt [s], dx/dt [m/s], lattices L, velocities Q, dimension D into out[0..4]. */
 int lbm_info(const lbm_ctx* ctx, double* out5);
@@ -332,20 +348,27 @@ int lbm_adjoint(lbm_ctx* ctx, const lbm_objective* obj, int n_steps, int ckpt_ev
  * on).  cfg supplies the physical parameters (its host arrays molar_mass,
  * D_ref, mu_ref, cv_factor, U0 and the reservoir fields are read; porosity,
  * X_init, T_init, P_init are not) and the stream.  The step is the two-pass
- * form on a D2Q9 lattice (nz == 1, M = 2 or 3, no surface mechanism) and is
- * issued asynchronously on cfg->stream.
+ * form on a D2Q9 lattice (nz == 1, M = 2 or 3, no surface mechanism), issued
+ * on cfg->stream.
  *
  * Its scratch (the macro fields of the first pass and a status word) lives
  * in one fixed array compiled into the library, lbm_noalloc_scratch_limit()
  * bytes of macro fields: (4 + M) * N * (8 or 4) bytes must fit, otherwise the
  * call returns LBM_ERR_ARG.  Every GPU that loads the library holds this
  * array until the process exits.  The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress) with that device current;
- * make that first call before any stream capture.  All calls share the array
- * and it keeps the last call's contents, so calls whose work overlaps on the
- * GPU race.  The status word is cleared at every call and is not reported.
- * Errors: LBM_ERR_ARG (invalid arguments, unsupported shape, too large),
- * LBM_ERR_CUDA (address look-up or launch failed).
+ * array's device address (cudaGetSymbolAddress) with that device current
+ * and keeps it for the rest of the process; make that first call before any
+ * stream capture, and do not call again after resetting the device
+ * (cudaDeviceReset unloads the array, so the kept address is stale).  All
+ * calls share the array and it keeps the last call's contents, so calls whose
+ * work overlaps on the GPU race.  The status word is cleared at every call;
+ * the call then waits for the step to finish on cfg->stream and reports it.
+ * The configuration is checked as lbm_create checks it (without the per-node
+ * input arrays, which this call does not read).
+ * Errors: LBM_ERR_ARG (invalid arguments, unsupported shape -- nz != 1, M
+ * other than 2 or 3, a surface mechanism -- or a lattice too large),
+ * LBM_ERR_NUMERIC (the step met a non-finite or non-positive state),
+ * LBM_ERR_CUDA (address look-up, launch or the wait failed).
  */
 int lbm_step_noalloc(const lbm_config* cfg, const void* pops_in, void* pops_out, const void* porosity,
                      const void* T_fixed);

@@ -52,6 +52,7 @@ void convert_params(const lbm::Params<double>& d, lbm::Params<R>& r) {
   r.T_thermo = (R)d.T_thermo; r.inv_T_ref = (R)d.inv_T_ref; r.Pref = (R)d.Pref;
   r.T_in[0] = (R)d.T_in[0]; r.T_in[1] = (R)d.T_in[1];
   r.kappa_thr = (R)d.kappa_thr;
+  r.wait_limit = d.wait_limit;
 }
 
 template <class R>
@@ -62,7 +63,11 @@ void convert_inlet(const lbm::InletTables<double>& d, lbm::InletTables<R>& r) {
   }
 }
 
-int validate(const lbm_config* c) {
+// Checks of the configuration itself; with fields, also the per-node input
+// arrays (porosity, X_init, T_init, P_init) that lbm_create reads.
+constexpr int kDefaultWaitLimit = 1 << 22;
+
+int validate(const lbm_config* c, bool fields = true) {
   if (!c) return fail(nullptr, LBM_ERR_ARG, "null config");
   if (c->nx < 1 || c->ny < 1 || c->nz < 1) return fail(nullptr, LBM_ERR_ARG, "lattice dimensions must be >= 1");
   if ((double)c->nx * c->ny * c->nz > 2.0e9) return fail(nullptr, LBM_ERR_ARG, "lattice too large");
@@ -81,8 +86,9 @@ int validate(const lbm_config* c) {
     return fail(nullptr, LBM_ERR_ARG, "dx, theta_max in (0,1), T_scale, T_ref, P_ref and Pr must be positive");
   if (c->knudsen && (!(c->pore_radius > 0) || !(c->tortuosity > 0)))
     return fail(nullptr, LBM_ERR_ARG, "Knudsen diffusion needs a positive pore radius and tortuosity");
-  if (!c->molar_mass || !c->D_ref || !c->mu_ref || !c->cv_factor || !c->U0 || !c->porosity || !c->X_init ||
-      !c->T_init || !c->P_init)
+  if (!c->molar_mass || !c->D_ref || !c->mu_ref || !c->cv_factor || !c->U0)
+    return fail(nullptr, LBM_ERR_ARG, "missing input array");
+  if (fields && (!c->porosity || !c->X_init || !c->T_init || !c->P_init))
     return fail(nullptr, LBM_ERR_ARG, "missing input array");
   for (int a = 0; a < c->M; ++a) {
     if (!(c->molar_mass[a] > 0) || !(c->mu_ref[a] >= 0) || !(c->cv_factor[a] > 0))
@@ -91,7 +97,7 @@ int validate(const lbm_config* c) {
       if (a != b && !(c->D_ref[a * c->M + b] > 0))
         return fail(nullptr, LBM_ERR_ARG, "binary diffusivities must be positive");
   }
-  size_t N = (size_t)c->nx * c->ny * c->nz;
+  size_t N = fields ? (size_t)c->nx * c->ny * c->nz : 0;
   for (size_t n = 0; n < N; ++n) {
     if (!(c->porosity[n] > 0) || !(c->porosity[n] <= 1)) return fail(nullptr, LBM_ERR_ARG, "porosity outside (0, 1]");
     if (!(c->T_init[n] > 0) || !(c->P_init[n] > 0)) return fail(nullptr, LBM_ERR_ARG, "non-positive T or P");
@@ -115,6 +121,8 @@ int validate(const lbm_config* c) {
 }  // namespace
 
 namespace lbm {
+// configuration checks of lbm_create without its per-node input arrays
+int validate_config(const lbm_config* c) { return validate(c, false); }
 
 // Lattice-unit parameters of a validated configuration.
 void make_params(const lbm_config* c, Params<double>& p, InletTables<double>& it, double& dt, double& cvel) {
@@ -150,6 +158,7 @@ void make_params(const lbm_config* c, Params<double>& p, InletTables<double>& it
   p.inv_T_ref = 1.0 / c->T_ref;
   p.Pref = c->P_ref / c2;
   p.kappa_thr = c->kappa_threshold > 0 ? c->kappa_threshold : 1e3;
+  p.wait_limit = kDefaultWaitLimit;
   std::memset(&it, 0, sizeof(it));
   const double* Xin[2] = {c->X_in_lo, c->X_in_hi};
   const double Tin[2] = {c->T_in_lo, c->T_in_hi}, Pin[2] = {c->P_in_lo, c->P_in_hi};
@@ -1058,6 +1067,15 @@ int lbm_step_host(lbm_ctx* x, const void* in_host, void* out_host, int n_steps) 
   if (e != cudaSuccess) return cuda_fail(x, e, "lbm_step_host download");
   x->free_recorded[P] = true;
   ++x->hcall;
+  return LBM_OK;
+}
+
+int lbm_set_wait_limit(lbm_ctx* x, int probes) {
+  if (!x) return LBM_ERR_ARG;
+  if (probes < 0) return fail(x, LBM_ERR_ARG, "negative wait limit");
+  x->pd.wait_limit = probes;
+  x->pf.wait_limit = probes;
+  drop_graphs(x);                    // captured launches carry the old parameters
   return LBM_OK;
 }
 

@@ -51,6 +51,7 @@ struct Params {
   R rho_in[2][MMAX];          // reservoir densities [kg/m^3]
   R T_in[2];
   R kappa_thr;
+  int wait_limit;             // probes per bounded device wait of the row-staged forms
 };
 
 // ---------------------------------------------------------------------------

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(TX, MINB)
   };
   // waits until row `row` has landed in its buffer; false if a bounded wait gave up
   auto landed = [&](int row) -> bool {
-    if (TMA && bulk) return mbar_wait(bar + buf_of(row), (uint32_t)(((row - (m0 - 1)) / NBUF) & 1));
+    if (TMA && bulk) return mbar_wait(bar + buf_of(row), (uint32_t)(((row - (m0 - 1)) / NBUF) & 1), p.wait_limit);
     cp_async_wait<PD - 1>();
     return true;
   };

@@ -15,7 +15,8 @@
 // up once per device with cudaGetSymbolAddress on the first call made while
 // that device is current, and reused afterwards.  All calls share the array
 // and it keeps the contents of the last call, so calls whose work overlaps on
-// the GPU (for example on two streams) race on it.
+// the GPU (for example on two streams) race on it.  Each call waits for its
+// step to finish and reports the step's status word in its return code.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -26,6 +27,7 @@
 
 namespace lbm {
 void make_params(const lbm_config* c, Params<double>& p, InletTables<double>& it, double& dt, double& cvel);
+int validate_config(const lbm_config* c);
 }
 
 namespace {
@@ -39,7 +41,11 @@ __device__ __align__(256) unsigned char g_step_scratch[kScratchBytes];
 std::mutex g_setup_mutex;
 unsigned char* g_scratch_addr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (set up once).
+// Device address of the scratch array on the current device, looked up once
+// per device (the first call made while that device is current) and reused.
+// A device reset (cudaDeviceReset) unloads the library's module, so the
+// cached address is no longer valid after one; callers that reset a device
+// must not call this entry point again in the same process.
 int scratch_address(unsigned char** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LBM_ERR_CUDA;
@@ -69,6 +75,7 @@ void to_precision(const lbm::Params<double>& d, lbm::Params<R>& r, const lbm::In
   r.T_thermo = (R)d.T_thermo; r.inv_T_ref = (R)d.inv_T_ref; r.Pref = (R)d.Pref;
   r.T_in[0] = (R)d.T_in[0]; r.T_in[1] = (R)d.T_in[1];
   r.kappa_thr = (R)d.kappa_thr;
+  r.wait_limit = d.wait_limit;
   for (int s = 0; s < 2; ++s) {
     for (int a = 0; a < lbm::MMAX; ++a) ri.rho[s][a] = (R)di.rho[s][a];
     ri.rho_sum[s] = (R)di.rho_sum[s]; ri.Rmix[s] = (R)di.Rmix[s]; ri.Umix[s] = (R)di.Umix[s]; ri.T[s] = (R)di.T[s];
@@ -107,7 +114,12 @@ int run(const lbm_config* c, const void* pops_in, void* pops_out, const void* po
     case 7: launch<R, 3, true>(p, it, a, s); break;
     default: return LBM_ERR_ARG;
   }
-  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+  if (cudaGetLastError() != cudaSuccess) return LBM_ERR_CUDA;
+  // the step's status word: bit 0 marks a non-finite or non-positive state
+  int st = 0;
+  if (cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return LBM_ERR_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return LBM_ERR_CUDA;
+  return (st & 1) ? LBM_ERR_NUMERIC : LBM_OK;
 }
 
 }  // namespace
@@ -119,15 +131,9 @@ size_t lbm_noalloc_scratch_limit(void) { return kScratchBytes - kStatusBytes; }
 int lbm_step_noalloc(const lbm_config* c, const void* pops_in, void* pops_out, const void* porosity,
                      const void* T_fixed) {
   if (!c || !pops_in || !pops_out || !porosity || !T_fixed || pops_in == pops_out) return LBM_ERR_ARG;
-  if (c->nz != 1 || c->nx < 1 || c->ny < 1 || (c->M != 2 && c->M != 3)) return LBM_ERR_ARG;
-  if (c->precision != LBM_FP64 && c->precision != LBM_FP32) return LBM_ERR_ARG;
-  if (c->bc_lo < 0 || c->bc_lo > 2 || c->bc_hi < 0 || c->bc_hi > 2) return LBM_ERR_ARG;
-  if ((c->bc_lo == LBM_BC_INLET || c->bc_hi == LBM_BC_INLET) && c->nx < 3) return LBM_ERR_ARG;
-  if (!c->molar_mass || !c->D_ref || !c->mu_ref || !c->cv_factor || !c->U0) return LBM_ERR_ARG;
-  if (!(c->dx > 0) || !(c->theta_max > 0) || !(c->T_scale > 0) || !(c->T_ref > 0) || !(c->P_ref > 0) ||
-      !(c->Pr > 0))
-    return LBM_ERR_ARG;
-  if (c->knudsen && !(c->pore_radius > 0 && c->tortuosity > 0)) return LBM_ERR_ARG;
+  // the checks of lbm_create that do not need its per-node input arrays
+  if (lbm::validate_config(c) != LBM_OK) return LBM_ERR_ARG;
+  if (c->nz != 1 || (c->M != 2 && c->M != 3) || c->S != 0) return LBM_ERR_ARG;
   const size_t rs = c->precision == LBM_FP64 ? 8 : 4;
   const size_t need = (size_t)(2 * 2 + c->M) * (size_t)c->nx * (size_t)c->ny * rs;
   if (need > lbm_noalloc_scratch_limit()) return LBM_ERR_ARG;   // lattice too large for the static scratch

@@ -118,6 +118,8 @@ def load(path: str = LIB_PATH):
     L.lbm_save.restype = ctypes.c_int
     L.lbm_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.lbm_load.restype = ctypes.c_int
+    L.lbm_set_wait_limit.argtypes = [vp, ctypes.c_int]
+    L.lbm_set_wait_limit.restype = ctypes.c_int
     _lib = L
     return L
 
@@ -268,6 +270,10 @@ class Lattice:
 
     def variant(self) -> int:
         return int(load().lbm_get_variant(self._h))
+
+    def set_wait_limit(self, probes: int):
+        """Bound of the row-staged forms' device waits (lbm_set_wait_limit)."""
+        self._check(load().lbm_set_wait_limit(self._h, int(probes)), "lbm_set_wait_limit")
 
     def autotune(self, steps: int = 5) -> int:
         best = ctypes.c_int(0)

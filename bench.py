@@ -529,6 +529,47 @@ def run_reference(args, ws, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+PROFILE_FORMS = ("slab", "slab_fp64", "anode", "anode_gather", "react", "batch", "adjoint")
+
+
+def profile_form(which):
+    """A few steps of one kernel form on a small case, for a profiler run
+    (ncu); prints nothing but "ok".
+    slab: the 512x512 slab in FP32, default form (TMA row march), 3 steps;
+    slab_fp64: the same in FP64;
+    anode: D3Q27 anode 64x32x32, six species, FP32, the default form (staged
+      with a gradient pass, variant 5), 3 steps; anode_gather: the staged form
+      that gathers its gradient inputs (variant 3);
+    react: the same lattice with the seeded surface mechanism, FP32, 3 steps;
+    batch: the 64-capillary sweep, FP32, staged persistent form (variant 7),
+      5 steps launched one by one (timing on, so no graph replay);
+    adjoint: 64x64 adjoint slab, FP32, 10 steps with checkpoints every 5."""
+    from paper_2409_02930_gb300 import lbm
+    if which in ("slab", "slab_fp64"):
+        g = lbm.Lattice(W.slab(512, 512, steps=3), precision=lbm.LBM_FP32 if which == "slab" else lbm.LBM_FP64)
+        g.step(3)
+        g.sync()
+    elif which in ("anode", "anode_gather"):
+        g = lbm.Lattice(W.anode3d(nx=64, ny=32, nz=32, steps=3), precision=lbm.LBM_FP32)
+        g.set_variant(5 if which == "anode" else 3)
+        g.step(3)
+        g.sync()
+    elif which == "react":
+        g = lbm.Lattice(W.anode3d_reactive(nx=64, ny=32, nz=32, steps=3), precision=lbm.LBM_FP32)
+        g.step(3)
+        g.sync()
+    elif which == "batch":
+        b = lbm.Batch(W.capillary_batch(), precision=lbm.LBM_FP32)
+        b.set_variant(7)
+        lbm.load().lbm_set_timing(b._h, 1)
+        b.step(5)
+        b.sync()
+    elif which == "adjoint":
+        g = lbm.Lattice(W.adjoint_slab(nx=64, ny=64, steps=10), precision=lbm.LBM_FP32)
+        g.adjoint(10, 5)
+    print("ok")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -543,7 +584,12 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / adjoint / reactive form lines")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--variant", type=int, default=None, help="kernel form (-1 two-pass, >= 0 fused tile); default: autotune")
+    ap.add_argument("--profile-form", choices=PROFILE_FORMS, default=None,
+                    help="run a few steps of one kernel form on a small case for a profiler, then exit")
     args = ap.parse_args()
+    if args.profile_form:
+        profile_form(args.profile_form)
+        return
     ws, rank, local = dist_init()
     if args.impl == "reference":
         out = run_reference(args, ws, rank)

@@ -22,10 +22,12 @@ _SRC = os.path.join(_HERE, "lbm_oracle.cpp")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liblbm_oracle.so")
 _LIB_DUAL = os.path.join(_BUILD, "liblbm_oracle_dual.so")
+_LIB_F32 = os.path.join(_BUILD, "liblbm_oracle_store_f32.so")
 LANES = 8            # derivative lanes of the dual-number build
 _lock = threading.Lock()
 _lib = None
 _lib_dual = None
+_lib_f32 = None
 
 BC_CODE = {"periodic": 0, "inlet": 1, "bounceback": 2}
 
@@ -80,6 +82,12 @@ def build_dual(force: bool = False) -> str:
     return _compile(_LIB_DUAL, [f"-DORACLE_DUAL={LANES}"], force)
 
 
+def build_store_f32(force: bool = False) -> str:
+    """Compile the measuring build that rounds every stored population to
+    single precision (arithmetic in double): the error floor of FP32 storage."""
+    return _compile(_LIB_F32, ["-DORACLE_STORE_F32"], force)
+
+
 def _declare(L):
     L.oc_create.restype = ctypes.c_void_p
     L.oc_create.argtypes = [ctypes.POINTER(OcConfig)]
@@ -116,6 +124,13 @@ def lib_dual():
     return _lib_dual
 
 
+def lib_store_f32():
+    global _lib_f32
+    if _lib_f32 is None:
+        _lib_f32 = _declare(ctypes.CDLL(build_store_f32()))
+    return _lib_f32
+
+
 def _ptr(a: np.ndarray):
     return a.ctypes.data_as(_dp)
 
@@ -127,10 +142,12 @@ def _f64(a) -> np.ndarray:
 class Oracle:
     """One oracle lattice built from a ``workloads.Workload``."""
 
-    def __init__(self, wl, nthreads: int = 0, dual: bool = False):
+    def __init__(self, wl, nthreads: int = 0, dual: bool = False, store_f32: bool = False):
         """dual=True uses the dual-number build: every quantity carries
-        ``LANES`` directional derivatives, seeded with ``set_tangents``."""
-        L = lib_dual() if dual else lib()
+        ``LANES`` directional derivatives, seeded with ``set_tangents``.
+        store_f32=True uses the measuring build whose stored populations are
+        rounded to single precision after every step (arithmetic in double)."""
+        L = lib_dual() if dual else (lib_store_f32() if store_f32 else lib())
         self._L = L
         self.wl = wl
         keep = {}

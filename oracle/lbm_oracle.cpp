@@ -93,6 +93,18 @@ inline real rmax(const real& a, const real& b) { return (a < b) ? b : a; }
 inline real rmin(const real& a, const real& b) { return (b < a) ? b : a; }
 #endif
 
+// Stored populations.  The plain build keeps them in double.  Built with
+// -DORACLE_STORE_F32 every stored population (the initial equilibria and the
+// output of every collision) is rounded to single precision while all the
+// arithmetic stays in double: the error that single-precision storage alone
+// imposes on a lattice, the floor any single-precision implementation sits
+// on (a measuring build of the test infrastructure, not a second method).
+#ifdef ORACLE_STORE_F32
+inline real stored(const real& v) { return (double)(float)v; }
+#else
+inline real stored(const real& v) { return v; }
+#endif
+
 namespace {
 
 const double R_UNIV = 8.314462618;      // J/(mol K)
@@ -934,15 +946,15 @@ void init_populations(Oracle* o) {
     real f[QMAX];
     for (int a = 0; a < o->M; ++a) {
       species_form(*o, ph, rho_a[a], xi, R_species(*o, a) * T, f);
-      for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, a, i, n)] = f[i];
+      for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, a, i, n)] = stored(f[i]);
     }
     species_form(*o, ph, rho, xi, R * T, f);
-    for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, o->M, i, n)] = f[i];
+    for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, o->M, i, n)] = stored(f[i]);
     if (o->energy) {
       real U = 0.0;
       for (int a = 0; a < o->M; ++a) U += (rho_a[a] / rho) * U_species(*o, a, T);
       energy_equilibrium(o->L, ph, rho, u, R * T, U, f);
-      for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, o->M + 1, i, n)] = f[i];
+      for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, o->M + 1, i, n)] = stored(f[i]);
     }
   }
 }
@@ -1136,7 +1148,7 @@ void oc_step(void* h, int nsteps) {
       real fout[(MMAX + 2) * QMAX];
       collide_at(o, n, fout);
       for (int l = 0; l < o->nl; ++l)
-        for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, l, i, n)] = fout[l * o->Q + i];
+        for (int i = 0; i < o->Q; ++i) o->pops[PIDX(*o, l, i, n)] = stored(fout[l * o->Q + i]);
     }
     if (o->S > 0) o->Xs.swap(o->Xs_new);
     o->steps_done++;

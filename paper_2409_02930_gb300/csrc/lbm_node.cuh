@@ -320,15 +320,34 @@ struct Transport {
         B[a][b] = (tiny ? R(0) : (ja[a * D + b] / s.rho_a[a] - s.u[b])) - R(0.5) * inv_tauk[a] * s.u[b];
     }
     used_fp64 = 0;
-    if (sizeof(R) == 4 && amax > p.kappa_thr * dmin) {
-      // condition bound above the threshold: solve in double
+    bool fp64_solve = false;
+    if constexpr (std::is_same<R, float>::value) fp64_solve = amax > p.kappa_thr * dmin;
+    if (fp64_solve) {
+      if constexpr (std::is_same<R, float>::value) {
+      // condition bound above the threshold: assemble and solve in double
+      // from the single-precision moments (the relaxation rates and the
+      // right-hand side's differences of velocities formed in double)
       double Ad[M][M], Bd[M][D];
+      const double Td = (double)s.T;
+      const double trd = Td * (double)p.inv_T_ref;
+      const double Cd = (double)s.m_mix * (double)p.RU * Td * (double)s.P / ((double)p.Pref * trd * sqrt(trd));
+      double itk[M];
+#pragma unroll
+      for (int a = 0; a < M; ++a)
+        itk[a] = p.knudsen ? (double)p.knc[a] * sqrt(Td) / (double)s.phi : 0.0;
 #pragma unroll
       for (int a = 0; a < M; ++a) {
+        double acc = 0.0;
 #pragma unroll
-        for (int b = 0; b < M; ++b) Ad[a][b] = (double)A[a][b];
+        for (int b = 0; b < M; ++b) acc += (double)s.Y[b] * Cd * (double)p.invDmm[a][b];
 #pragma unroll
-        for (int b = 0; b < D; ++b) Bd[a][b] = (double)B[a][b];
+        for (int b = 0; b < M; ++b)
+          Ad[a][b] = (a == b) ? 1.0 + 0.5 * acc + 0.5 * itk[a] : -0.5 * (double)s.Y[b] * Cd * (double)p.invDmm[a][b];
+        bool tiny = s.rho_a[a] < R(1e-14) * s.rho_s || !(sabs[a] <= R(1e4) * s.phi * s.rho_a[a]);
+#pragma unroll
+        for (int b = 0; b < D; ++b)
+          Bd[a][b] = (tiny ? 0.0 : ((double)ja[a * D + b] / (double)s.rho_a[a] - (double)s.u[b])) -
+                     0.5 * itk[a] * (double)s.u[b];
       }
       gauss<double>(Ad, Bd);
 #pragma unroll
@@ -336,6 +355,7 @@ struct Transport {
 #pragma unroll
         for (int b = 0; b < D; ++b) V[a][b] = (R)Bd[a][b];
       used_fp64 = 1;
+      }
     } else {
       gauss<R>(A, B);
 #pragma unroll

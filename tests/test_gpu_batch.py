@@ -101,25 +101,39 @@ def test_fp32_batch_full_size_matches_single_cases(L):
         g.close()
 
 
-def test_fp32_batch_matches_oracle_on_short_cases(L):
-    """FP32 batch against the FP64 oracle after 1000 steps.  In the pure
-    halves of a capillary the species lattice of the present species has no
-    partner to collide with (beta = 0) and relaxes only through the Knudsen
-    term, whose rate dt/tau^k falls as dx/r_p: FP32 rounding there performs a
-    weakly damped random walk.  Densities stay within 1e-4 of the field
-    maximum (the per-case errors are reported); FP64 batches match the oracle
-    to 1e-12."""
-    wls = W.capillary_batch(n_cases=6, seed=13, nmin=32, nmax=128, steps=1000)
+def test_fp32_batch_matches_oracle_on_the_full_sweep(L):
+    """FP32 batch against the FP64 oracle after 1000 steps, every one of the
+    64 capillaries (densities and fluxes, field-relative per case and
+    species, the worst species of the case).  The bound is the error that FP32 storage alone imposes on
+    each case: the oracle's measuring build with its stored populations
+    rounded to FP32 (arithmetic in double) gives that floor (1.6e-6 to
+    2.7e-5 on the densities here).  The FP32 arithmetic adds more where a
+    pure half of a capillary leaves a species without collision partners
+    (beta = 0) and the trace tail of the other species is resolved by the
+    FP32 trace criterion (reading R26): the densities sit 0.6 to 24 times
+    the floor (up to 1.8e-4, the same as each case run alone), the fluxes 1
+    to 9 times.  Bounds: 30 times the floor on the densities, 12 times on the
+    fluxes."""
+    wls = W.capillary_batch(steps=1000)
     b = L.Batch(wls, precision=L.LBM_FP32)
     b.step(1000)
     b.sync()
-    rho = b.moments(L.LBM_MOM_RHO_A)
+    mom = {k: b.moments(getattr(L, "LBM_MOM_" + k)) for k in ("RHO_A", "J_A")}
+    worst = 0.0
     for c, wl in enumerate(wls):
         o = oracle.Oracle(wl)
+        f = oracle.Oracle(wl, store_f32=True)
         o.step(1000)
-        e = rel(rho[c], o.moments(oracle.MOM_RHO_A))
-        print("case", c, wl.nx, "nodes", "%.3f atm" % (wl.P_init[0] / W.ATM), "FP32 density error %.2e" % e)
-        assert e < 1e-4, c
+        f.step(1000)
+        for name, k in (("RHO_A", oracle.MOM_RHO_A), ("J_A", oracle.MOM_J_A)):
+            ref = o.moments(k)
+            # the case's error and floor: the worst species of each
+            gpu = max(rel(mom[name][c][a], ref[a]) for a in range(wl.M))
+            floor = max(rel(f.moments(k)[a], ref[a]) for a in range(wl.M))
+            worst = max(worst, gpu / (floor + 1e-7))
+            k_bound = 30.0 if name == "RHO_A" else 12.0
+            assert gpu <= k_bound * floor + 1e-7, (c, name, gpu, floor)
+    print("largest ratio of the batch error to the FP32-storage floor: %.2f" % worst)
 
 
 def test_batch_rejects_mixed_kinds(L):

@@ -57,58 +57,35 @@ def test_slab_512_fp32_autotuned(L):
     assert e < 1e-5 and ef < 1e-5 and eT < 1e-5
 
 
-def oracle_sensitivity(wl, steps, moments):
-    """How far the oracle moves from itself when its initial populations are
-    perturbed at the rounding level (1e-16 relative): the rounding
-    sensitivity of the discrete method on this case (the trace-species switch
-    of reading R11 turns rounding differences into small jumps)."""
-    a = oracle.Oracle(wl)
-    b = oracle.Oracle(wl)
-    p = b.pops()
-    b.set_pops(p * (1 + 1e-16 * np.random.default_rng(0).standard_normal(p.shape)))
-    a.step(steps)
-    b.step(steps)
-    return {k: (a.moments(getattr(oracle, "MOM_" + k)), b.moments(getattr(oracle, "MOM_" + k))) for k in moments}
-
-
 def test_batch_64_capillaries_fp64(L):
-    """Every case within the FP64 bound 1e-12, or within ten times the
-    oracle's own rounding sensitivity on that case when that is larger
-    (some low-pressure capillaries move 7e-12 from a 1e-16 perturbation).
-    Densities field-relative; species fluxes against max rho_a x lattice
-    speed; velocity in lattice units.  The worst population error is
-    reported."""
+    """Every case of the 64-capillary FP64 batch against the oracle after 100
+    steps (two graph replays): populations of every lattice and the moments
+    rho_a, rho (field-relative), species fluxes (against max rho_a x lattice
+    speed) and velocity (lattice units) within 1e-12.  The oracle's own
+    rounding sensitivity on these cases (its run restarted from populations
+    perturbed by 1e-16) is at most 1.2e-14 in the densities."""
     wls = W.capillary_batch()
     b = L.Batch(wls, precision=L.LBM_FP64)
-    b.step(100)                       # two graph replays
+    b.step(100)
     b.sync()
     pops = b.populations()
     keys = ("RHO_A", "J_A", "RHO", "U")
     mom = {k: b.moments(getattr(L, "LBM_MOM_" + k)) for k in keys}
-
-    def errs(x, ref):
-        return {"RHO_A": rel(x["RHO_A"], ref["RHO_A"]), "RHO": rel(x["RHO"], ref["RHO"]),
-                "J_A": float(np.max(np.abs(x["J_A"] - ref["J_A"])) / np.max(ref["RHO_A"])),
-                "U": float(np.max(np.abs(x["U"] - ref["U"])))}
-
-    worst_ratio, worst, worst_p = 0.0, None, 0.0
+    worst = (0.0, None)
     for c, wl in enumerate(wls):
-        pairs = oracle_sensitivity(wl, 100, keys)
-        ref = {k: v[0] for k, v in pairs.items()}
-        sens = errs({k: v[1] for k, v in pairs.items()}, ref)
-        e = errs({k: mom[k][c] for k in keys}, ref)
-        for k in keys:
-            bound = max(1e-12, 10.0 * sens[k])
-            if e[k] / bound > worst_ratio:
-                worst_ratio, worst = e[k] / bound, (c, k, e[k], sens[k])
         o = oracle.Oracle(wl)
         o.step(100)
+        ref = {k: o.moments(getattr(oracle, "MOM_" + k)) for k in keys}
+        e = {"RHO_A": rel(mom["RHO_A"][c], ref["RHO_A"]), "RHO": rel(mom["RHO"][c], ref["RHO"]),
+             "J_A": float(np.max(np.abs(mom["J_A"][c] - ref["J_A"])) / np.max(ref["RHO_A"])),
+             "U": float(np.max(np.abs(mom["U"][c] - ref["U"])))}
         po = o.pops()
-        for l in range(b.L):
-            worst_p = max(worst_p, rel(pops[c][l], po[l]))
-    print("64 capillaries FP64, 100 steps: worst (case, moment, error, oracle sensitivity)", worst,
-          "ratio to bound %.3f" % worst_ratio, "worst population error %.2e" % worst_p)
-    assert worst_ratio < 1.0, worst
+        e.update({f"pop{l}": rel(pops[c][l], po[l]) for l in range(b.L)})
+        for k, v in e.items():
+            if v > worst[0]:
+                worst = (v, (c, k))
+        assert max(e.values()) < 1e-12, (c, e)
+    print("64 capillaries FP64, 100 steps: worst error %.2e at (case, field) %s" % worst)
 
 
 def test_anode_full_size_fp32_default_form(L):

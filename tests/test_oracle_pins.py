@@ -556,3 +556,21 @@ def test_bounceback_walls_do_not_slip():
         assert abs(jx) < 1e-12 * abs(jy[-1])
     assert all(b < a for a, b in zip(jy, jy[1:]))
     assert jy[-1] < 0.9 * jy[0]
+
+
+def test_store_f32_build_rounds_only_the_stored_populations():
+    """The measuring build (stored populations rounded to FP32, arithmetic in
+    double) stores FP32-representable values and, from the same state, one
+    step away differs from the plain build by one FP32 rounding of each
+    stored population and nothing else."""
+    wl = W.slab(nx=16, ny=12, steps=1)
+    f = oracle.Oracle(wl, store_f32=True)
+    p = oracle.Oracle(wl)
+    p0 = f.pops()
+    assert np.array_equal(p0, p0.astype(np.float32).astype(np.float64))
+    p.set_pops(p0)
+    p.step(1)
+    f.step(1)
+    a, b = f.pops(), p.pops()
+    assert np.array_equal(a, b.astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(a - b) / np.abs(b)) <= 2.0 ** -24

@@ -185,13 +185,13 @@ def large_lattice_line(stream, torch, lbm, nx=2048, ny=2048, steps=50, warmup=5)
     twelve times the L2: steps back to back with no flush, so every step
     reads its populations from HBM and its write-back lands inside the timed
     window.  Kernel time per launch from the library's own events on its
-    stream, roofline against the algorithmic bytes."""
+    stream, roofline against the algorithmic bytes.  The lattice runs in the
+    default form of a new context, the one the ncu traffic was taken on."""
     import ctypes
     sp = ctypes.c_void_p(stream.cuda_stream)
     wl = W.slab(nx=nx, ny=ny, steps=steps, name=f"slab_{nx}x{ny}")
     g = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
-    variant = g.autotune(3)
-    g.set_variant(variant)
+    variant = g.variant()                 # the default form (TMA row march, variant 8)
     g.step(warmup)
     lib = lbm.load()
     torch.cuda.synchronize()
@@ -529,7 +529,7 @@ def run_reference(args, ws, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-PROFILE_FORMS = ("slab", "slab_fp64", "anode", "anode_gather", "react", "batch", "adjoint")
+PROFILE_FORMS = ("slab", "slab_fp64", "slab2048", "anode", "anode_gather", "react", "batch", "adjoint")
 
 
 def profile_form(which):
@@ -537,6 +537,7 @@ def profile_form(which):
     (ncu); prints nothing but "ok".
     slab: the 512x512 slab in FP32, default form (TMA row march), 3 steps;
     slab_fp64: the same in FP64;
+    slab2048: the 2048x2048 slab in FP32 (the back-to-back line), 3 steps;
     anode: D3Q27 anode 64x32x32, six species, FP32, the default form (staged
       with a gradient pass, variant 5), 3 steps; anode_gather: the staged form
       that gathers its gradient inputs (variant 3);
@@ -545,8 +546,9 @@ def profile_form(which):
       5 steps launched one by one (timing on, so no graph replay);
     adjoint: 64x64 adjoint slab, FP32, 10 steps with checkpoints every 5."""
     from paper_2409_02930_gb300 import lbm
-    if which in ("slab", "slab_fp64"):
-        g = lbm.Lattice(W.slab(512, 512, steps=3), precision=lbm.LBM_FP32 if which == "slab" else lbm.LBM_FP64)
+    if which in ("slab", "slab_fp64", "slab2048"):
+        side = 2048 if which == "slab2048" else 512
+        g = lbm.Lattice(W.slab(side, side, steps=3), precision=lbm.LBM_FP64 if which == "slab_fp64" else lbm.LBM_FP32)
         g.step(3)
         g.sync()
     elif which in ("anode", "anode_gather"):

@@ -71,6 +71,8 @@ extern "C" {
 #define LBM_MOM_N_A   7       /* molar fluxes rho_a (u + V_a)/m_a, [M][D][N], mol m^-2 s^-1 */
 #define LBM_MOM_XS    8       /* surface coverages X^(s), [S][N] (eq:surfaceMoleFractions) */
 #define LBM_MOM_RHO_S 9       /* sum_a rho_a, [N], kg/m^3 (eq:rhoSpec) */
+#define LBM_MOM_CURRENT 10    /* volumetric current of the TPB steps, [N], A per m^3 of porous medium
+                                 (eq:volumetricCurrent; zero without edge steps) */
 
 typedef struct lbm_ctx lbm_ctx;
 
@@ -123,6 +125,22 @@ typedef struct lbm_config {
   const double* surf_U0;       /* [S] molar internal energy at T_thermo [J/mol] */
   const double* Xs_init;       /* [S] initial coverages */
   void* stream;                /* cudaStream_t for all work of the context */
+  /* electrochemistry (Sec. 4): steps on the triple-phase boundary (TPB), an
+   * edge whose length per volume of porous medium is l_tpb.  An edge step's
+   * rate is per unit TPB length, involves adsorbates only, changes the
+   * coverages by nu l_tpb/(a_s Gamma) per extent (eq:totalSurfaceReactionRate)
+   * and releases n_el electrons; its constant carries the factor
+   * exp(beta_ct n_el F dphi/(R_U T)).  The volumetric current is
+   * F l_tpb (electrons per TPB length and second) (eq:volumetricCurrent); the
+   * fluid energy gains the ohmic heat (a_s/l_tpb) I^2 resistivity dx and
+   * loses the electric power |dphi| I (Sec. 4.2).  edge == NULL: no edge
+   * steps (the fields below are then not read). */
+  const int* edge;             /* [R] 1 for a TPB step, 0 for a surface step */
+  const double* n_el;          /* [R] electrons released by each step */
+  double l_tpb;                /* TPB length per volume [1/m^2] */
+  double beta_ct;              /* charge-transfer symmetry factor */
+  double resistivity;          /* electrolyte resistivity [Ohm m] */
+  double dphi;                 /* Phi_electrode - Phi_electrolyte [V] */
 } lbm_config;
 
 /*

@@ -32,7 +32,7 @@ _lib_f32 = None
 BC_CODE = {"periodic": 0, "inlet": 1, "bounceback": 2}
 
 # moment selectors (same numbering as the library's public header)
-MOM_RHO_A, MOM_J_A, MOM_RHO, MOM_U, MOM_T, MOM_P, MOM_V_A, MOM_N_A, MOM_XS, MOM_RHO_S = range(10)
+MOM_RHO_A, MOM_J_A, MOM_RHO, MOM_U, MOM_T, MOM_P, MOM_V_A, MOM_N_A, MOM_XS, MOM_RHO_S, MOM_CURRENT = range(11)
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -57,6 +57,9 @@ class OcConfig(ctypes.Structure):
         ("gamma", ctypes.c_double), ("a_s", ctypes.c_double),
         ("surf_molar_mass", _dp), ("surf_cv_factor", _dp), ("surf_U0", _dp),
         ("gas_U0_molar", _dp), ("Xs_init", _dp), ("U_init", _dp),
+        ("edge", ctypes.POINTER(ctypes.c_int)), ("n_el", _dp),
+        ("l_tpb", ctypes.c_double), ("beta_ct", ctypes.c_double), ("resistivity", ctypes.c_double),
+        ("dphi", ctypes.c_double),
     ]
 
 
@@ -192,6 +195,13 @@ class Oracle:
             c.surf_U0 = arr("Us0", mech.surf_U0)
             c.gas_U0_molar = arr("Ug0", mech.gas_U0_molar)
             c.Xs_init = arr("Xs", mech.Xs_init)
+            if getattr(mech, "edge", None) is not None:
+                e = np.ascontiguousarray(np.asarray(mech.edge, dtype=np.int32))
+                keep["edge"] = e
+                c.edge = e.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+                c.n_el = arr("nel", mech.n_el)
+                c.l_tpb, c.beta_ct = mech.l_tpb, mech.beta_ct
+                c.resistivity, c.dphi = mech.resistivity, mech.dphi
         else:
             c.S, c.R = 0, 0
         if getattr(wl, "U_init", None) is not None:
@@ -236,7 +246,7 @@ class Oracle:
 
     def diag(self, which: int) -> np.ndarray:
         shapes = {0: (self.M, 3, self.N), 1: (3, self.N), 2: (self.N,), 3: (self.N,),
-                  4: (self.N,), 5: (self.M, self.N)}
+                  4: (self.N,), 5: (self.M, self.N), 6: (self.N,)}
         out = np.empty(shapes[which])
         self._L.oc_get_diag(self._h, which, _ptr(out))
         return out
@@ -247,7 +257,7 @@ class Oracle:
         S = self.wl.mechanism.S if self.wl.mechanism is not None else 0
         shapes = {MOM_RHO_A: (M, N), MOM_J_A: (M, D, N), MOM_RHO: (N,), MOM_U: (D, N),
                   MOM_T: (N,), MOM_P: (N,), MOM_V_A: (M, D, N), MOM_N_A: (M, D, N),
-                  MOM_XS: (S, N), MOM_RHO_S: (N,)}
+                  MOM_XS: (S, N), MOM_RHO_S: (N,), MOM_CURRENT: (N,)}
         out = np.empty(shapes[which])
         if lane is None:
             self._L.oc_moments(self._h, which, _ptr(out))

@@ -310,6 +310,13 @@ struct oc_config {
   const double* gas_U0_molar;     // [M] J/mol
   const double* Xs_init;          // [S]
   const double* U_init;           // [3*N] initial velocity [m/s] (null: at rest)
+  // electrochemistry (Sec. 4): triple-phase-boundary (edge) steps
+  const int* edge;                // [R] 1: the step runs on the TPB edge (null: none)
+  const double* n_el;             // [R] electrons produced by the step
+  double l_tpb;                   // TPB length per volume of porous medium [1/m^2]
+  double beta_ct;                 // charge-transfer symmetry factor
+  double resistivity;             // electrolyte resistivity Omega [Ohm m]
+  double dphi;                    // Phi_electrode - Phi_electrolyte [V]
 };
 
 }  // extern "C"
@@ -342,11 +349,13 @@ struct Oracle {
   int S, Rn;
   double nu_g[RMAX][MMAX], nu_s[RMAX][SMAX], Apre[RMAX], Ea[RMAX];
   real gamma, a_s, ms[SMAX], cvs[SMAX], Us0[SMAX], Ug0[MMAX];
+  int edge[RMAX];
+  double nel[RMAX], l_tpb, beta_ct, resist, dphi;
   // state
   std::vector<real> pops, pulled, phi, Tfix, Xs, Xs_new;
   std::vector<Macro> mac;
   // diagnostics of the last collision
-  std::vector<real> dg_V, dg_Fk, dg_omega, dg_omega1, dg_T, dg_P, dg_rhodot, dg_kappa;
+  std::vector<real> dg_V, dg_Fk, dg_omega, dg_omega1, dg_T, dg_P, dg_rhodot, dg_kappa, dg_current;
   long steps_done;
   // initial fields (kept to rebuild the initial populations)
   std::vector<double> X0, T0, P0, U0i, Xs_init0;
@@ -457,7 +466,7 @@ void compute_macro(const Oracle& o, const real* fpop /* [nl][Q] */, real phi, re
 // eq:totalFluidReactionRate / eq:molarToMassRates) and the new coverages.
 // ---------------------------------------------------------------------------
 void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhodot_f,
-                    real* Xs1, real& dU_fluid_volumetric);
+                    real* Xs1, real& dU_fluid_volumetric, real& current);
 
 // ---------------------------------------------------------------------------
 // One node's collision (a4 .. a9).  fin: streamed populations [nl][Q];
@@ -543,7 +552,9 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   real rhodot[MMAX];
   for (int a = 0; a < M; ++a) rhodot[a] = 0.0;
   real dU_src = 0.0;
-  if (o.S > 0) surface_source(o, m, Xs0, rhodot, Xs1, dU_src);
+  real Iv = 0.0;
+  if (o.S > 0) surface_source(o, m, Xs0, rhodot, Xs1, dU_src, Iv);
+  const_cast<Oracle&>(o).dg_current[n] = Iv;
   for (int a = 0; a < M; ++a) const_cast<Oracle&>(o).dg_rhodot[(size_t)a * o.N + n] = rhodot[a];
 
   // --- species collision (a7): eqn:finalNumericalEquationsReactive ----------
@@ -806,9 +817,16 @@ void gradients(const Oracle& o, int n, Grad& gr) {
 // Rates of progress r_k [mol m^-2 s^-1] by mass action with Arrhenius
 // constants k = A exp(-Ea/(R_U T)) (reading R15).  c_gas in mol/m^3 (fluid),
 // theta = surface concentration Gamma X^(s) in mol/m^2.
+// Edge (triple-phase-boundary) steps, Sec. 4: their rates are per unit TPB
+// length [mol m^-1 s^-1], and a step that releases n electrons has its
+// constant raised by exp(beta n F (Phi_electrode - Phi_electrolyte)/(R_U T))
+// (charge transfer with symmetry factor beta; reading R29).
+const double FARADAY = 96485.33212;     // C/mol
+
 void mass_action_rates(const Oracle& o, real T, const real* cg, const real* cs, real* r) {
   for (int k = 0; k < o.Rn; ++k) {
     real kr = o.Apre[k] * r_exp(-o.Ea[k] / (R_UNIV * T));
+    if (o.edge[k]) kr *= r_exp(o.beta_ct * o.nel[k] * FARADAY * o.dphi / (R_UNIV * T));
     real v = kr;
     for (int a = 0; a < o.M; ++a)
       if (o.nu_g[k][a] < 0) v *= r_pow(rmax(cg[a], 0.0), -o.nu_g[k][a]);
@@ -822,7 +840,7 @@ void mass_action_rates(const Oracle& o, real T, const real* cg, const real* cs, 
 // xi = dt * r(c_gas0 + (a_s/phi) nu_g^T xi, theta0 + nu_s^T xi), solved by
 // Newton with a finite-difference-free analytic Jacobian of mass action.
 void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhodot_f,
-                    real* Xs1, real& dU_fluid_volumetric) {
+                    real* Xs1, real& dU_fluid_volumetric, real& current) {
   const int M = o.M, S = o.S, Rn = o.Rn;
   const real T = m.T;
   const real dtp = o.dt;                        // physical seconds
@@ -832,10 +850,14 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
   real xi[RMAX];
   for (int k = 0; k < Rn; ++k) xi[k] = 0.0;
   real scale = o.a_s / m.phi;                   // surface area per fluid volume
+  // surface concentration change per extent: 1 for a surface step, l_TPB/a^(s)
+  // for an edge step (eq:totalSurfaceReactionRate), whose extent is per TPB length
+  real es[RMAX];
+  for (int k = 0; k < Rn; ++k) es[k] = o.edge[k] ? o.l_tpb / o.a_s : 1.0;
   for (int it = 0; it < 30; ++it) {
     real cg[MMAX], cs[SMAX];
     for (int a = 0; a < M; ++a) { cg[a] = cg0[a]; for (int k = 0; k < Rn; ++k) cg[a] += scale * o.nu_g[k][a] * xi[k]; }
-    for (int s = 0; s < S; ++s) { cs[s] = cs0[s]; for (int k = 0; k < Rn; ++k) cs[s] += o.nu_s[k][s] * xi[k]; }
+    for (int s = 0; s < S; ++s) { cs[s] = cs0[s]; for (int k = 0; k < Rn; ++k) cs[s] += o.nu_s[k][s] * es[k] * xi[k]; }
     real r[RMAX];
     mass_action_rates(o, T, cg, cs, r);
     real Fv[RMAX], J[RMAX * RMAX];
@@ -847,7 +869,7 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
         for (int a = 0; a < M; ++a)
           if (o.nu_g[k][a] < 0 && cg[a] > 0) d += r[k] * (-o.nu_g[k][a]) / cg[a] * scale * o.nu_g[l][a];
         for (int s = 0; s < S; ++s)
-          if (o.nu_s[k][s] < 0 && cs[s] > 0) d += r[k] * (-o.nu_s[k][s]) / cs[s] * o.nu_s[l][s];
+          if (o.nu_s[k][s] < 0 && cs[s] > 0) d += r[k] * (-o.nu_s[k][s]) / cs[s] * o.nu_s[l][s] * es[l];
         J[k * Rn + l] = (k == l ? 1.0 : 0.0) - dtp * d;
       }
     // Gaussian elimination with partial pivoting on J dxi = -F
@@ -883,7 +905,7 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
     }
     for (int s = 0; s < S; ++s) {
       real d = 0.0;
-      for (int k = 0; k < Rn; ++k) d += o.nu_s[k][s] * dxi[k];
+      for (int k = 0; k < Rn; ++k) d += o.nu_s[k][s] * es[k] * dxi[k];
       if (cs[s] >= 0.0 && cs[s] + d < 0.0) alpha = rmin(alpha, 0.9 * cs[s] / (-d));
     }
     real dmax = 0.0, xmax = 0.0;
@@ -903,9 +925,14 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
   }
   for (int s = 0; s < S; ++s) {
     real dn = 0.0;
-    for (int k = 0; k < Rn; ++k) dn += o.nu_s[k][s] * xi[k];
-    Xs1[s] = Xs0[s] + dn / o.gamma;               // eq:totalSurfaceReactionRate (no edge term)
+    for (int k = 0; k < Rn; ++k) dn += o.nu_s[k][s] * es[k] * xi[k];
+    Xs1[s] = Xs0[s] + dn / o.gamma;               // eq:totalSurfaceReactionRate (surface and edge terms)
   }
+  // volumetric current (eq:volumetricCurrent): I = F l_TPB (electrons per TPB length per second)
+  real ne = 0.0;
+  for (int k = 0; k < Rn; ++k)
+    if (o.edge[k]) ne += o.nel[k] * xi[k];
+  current = FARADAY * o.l_tpb * ne / dtp;         // A per m^3 of porous medium
   // Unified internal energy (eq:temperatureCell, eq:InternalEnergyCell_PC): at
   // fixed temperature the fluid gains what the adsorbed phase loses; molar
   // internal energies U_s(T) = U0_s + cv_s R_U (T - T_thermo).
@@ -913,10 +940,19 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
   for (int s = 0; s < S; ++s) {
     real Us = o.Us0[s] + o.cvs[s] * R_UNIV * (T - o.cfg.T_thermo);
     real dn = 0.0;
-    for (int k = 0; k < Rn; ++k) dn += o.nu_s[k][s] * xi[k];
+    for (int k = 0; k < Rn; ++k) dn += o.nu_s[k][s] * es[k] * xi[k];
     dUs += o.a_s * dn * Us;                       // J/m^3 of REV
   }
-  dU_fluid_volumetric = -dUs / (o.cvel * o.cvel); // lattice energy units (J/kg -> (dx/dt)^2)
+  // electric power leaves, ohmic heat stays (Sec. 4.2, reading R28):
+  // P_elec = |Phi_electrode - Phi_electrolyte| I, P_Omega = (a^(s)/l_TPB) I^2 Omega dx,
+  // source over the step (P_Omega - P_elec) dt
+  real U_source = 0.0;
+  if (o.l_tpb > 0.0) {
+    const real P_elec = std::fabs(o.dphi) * current;
+    const real P_ohm = (o.a_s / o.l_tpb) * current * current * o.resist * o.cfg.dx;
+    U_source = (P_ohm - P_elec) * dtp;
+  }
+  dU_fluid_volumetric = (-dUs + U_source) / (o.cvel * o.cvel); // lattice energy units (J/kg -> (dx/dt)^2)
 }
 
 }  // namespace
@@ -981,8 +1017,9 @@ void moments_lane(Oracle* o, int which, int lane, double* out) {
   }
   stream(*o);
   compute_all_macro(*o);
-  if (which == 6 || which == 7) {
-    // the diffusion velocities need the collision's transport coefficients;
+  if (which == 6 || which == 7 || which == 10) {
+    // the diffusion velocities and the current need the collision's transport
+    // coefficients and surface source;
     // run the collision into a scratch buffer and read its diagnostics
     std::vector<real> keep_xs = o->Xs_new;
 #pragma omp parallel for schedule(static)
@@ -1009,6 +1046,7 @@ void moments_lane(Oracle* o, int which, int lane, double* out) {
                     comp(m.rho_a[a] * (m.u[al] + o->dg_V[((size_t)a * 3 + al) * N + n]) * o->cvel / o->m[a], lane);
               break;
       case 9: out[n] = comp(m.rho_s, lane); break;
+      case 10: out[n] = comp(o->dg_current[n], lane); break;
       default: break;
     }
   }
@@ -1068,7 +1106,13 @@ void* oc_create(const oc_config* c) {
       for (int s = 0; s < o->S; ++s) o->nu_s[k][s] = c->nu_surf[k * o->S + s];
       o->Apre[k] = c->A_pre[k];
       o->Ea[k] = c->Ea[k];
+      o->edge[k] = c->edge ? c->edge[k] : 0;
+      o->nel[k] = c->n_el ? c->n_el[k] : 0.0;
     }
+    o->l_tpb = c->l_tpb;
+    o->beta_ct = c->beta_ct;
+    o->resist = c->resistivity;
+    o->dphi = c->dphi;
     o->gamma = c->gamma;
     o->a_s = c->a_s;
     for (int s = 0; s < o->S; ++s) {
@@ -1091,6 +1135,7 @@ void* oc_create(const oc_config* c) {
   o->dg_omega1.assign(N, 0.0);
   o->dg_kappa.assign(N, 0.0);
   o->dg_rhodot.assign((size_t)MMAX * N, 0.0);
+  o->dg_current.assign(N, 0.0);
   if (o->S > 0) {
     o->Xs.assign((size_t)o->S * N, 0.0);
     for (int s = 0; s < o->S; ++s)
@@ -1188,6 +1233,7 @@ void oc_get_diag(void* h, int which, double* out) {
     case 3: v = &o->dg_omega1; cnt = o->N; break;
     case 4: v = &o->dg_kappa; cnt = o->N; break;
     case 5: v = &o->dg_rhodot; cnt = (size_t)o->M * o->N; break;
+    case 6: v = &o->dg_current; cnt = o->N; break;
     default: return;
   }
   for (size_t k = 0; k < cnt; ++k) out[k] = comp((*v)[k], -1);

@@ -114,6 +114,8 @@ int validate(const lbm_config* c, bool fields = true) {
         !c->Xs_init || !(c->gamma > 0) || !(c->a_s > 0))
       return fail(nullptr, LBM_ERR_ARG, "incomplete surface mechanism");
     if (!c->energy) return fail(nullptr, LBM_ERR_ARG, "a surface mechanism needs the energy lattice");
+    if (c->edge && (!c->n_el || !(c->l_tpb > 0) || !(c->beta_ct >= 0) || !(c->resistivity >= 0)))
+      return fail(nullptr, LBM_ERR_ARG, "TPB steps need electron counts, a positive TPB length and beta >= 0");
   }
   return LBM_OK;
 }
@@ -224,7 +226,19 @@ static int setup_surface(lbm_ctx* x, const lbm_config* c) {
     h.nre[k] = nr;
     h.A[k] = c->A_pre[k];
     h.Ea[k] = c->Ea[k];
+    h.edge[k] = c->edge ? (c->edge[k] != 0) : 0;
+    h.nel[k] = c->edge ? c->n_el[k] : 0.0;
+    if (h.edge[k])
+      for (int a = 0; a < c->M; ++a)
+        if (c->nu_gas[k * c->M + a] != 0) return fail(nullptr, LBM_ERR_ARG, "a TPB step involves adsorbates only");
   }
+  if (c->edge) {
+    h.l_tpb = c->l_tpb;
+    h.beta_ct = c->beta_ct;
+    h.resist = c->resistivity;
+    h.dphi = c->dphi;
+  }
+  h.dx = c->dx;
   h.gamma = c->gamma;
   h.a_s = c->a_s;
   for (int q = 0; q < c->S; ++q) {
@@ -238,7 +252,7 @@ static int setup_surface(lbm_ctx* x, const lbm_config* c) {
   cudaError_t e = cudaMalloc(&x->mech, sizeof(lbm::MechDev));
   if (e == cudaSuccess) e = cudaMalloc(&x->Xs[0], (size_t)c->S * N * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&x->Xs[1], (size_t)c->S * N * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&x->rsrc, (size_t)(c->M + 1) * N * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&x->rsrc, (size_t)(c->M + 2) * N * sizeof(double));
   if (e != cudaSuccess) return fail(nullptr, LBM_ERR_ALLOC, "surface state allocation failed");
   std::vector<double> xs((size_t)c->S * N);
   for (int q = 0; q < c->S; ++q)
@@ -856,6 +870,36 @@ int lbm_moments(lbm_ctx* x, int which, void* out, size_t bytes, int out_on_devic
     case LBM_MOM_J_A: case LBM_MOM_V_A: case LBM_MOM_N_A: count = M * D * N; break;
     case LBM_MOM_RHO: case LBM_MOM_T: case LBM_MOM_P: case LBM_MOM_RHO_S: count = N; break;
     case LBM_MOM_U: count = D * N; break;
+    case LBM_MOM_CURRENT: {
+      // the surface-source pass of the next step, run on the current state
+      // into the scratch it owns (sources, macro fields, next coverages)
+      count = N;
+      if (bytes < count * sizeof(double)) return fail(x, LBM_ERR_ARG, "output buffer too small");
+      cudaError_t e2 = cudaSuccess;
+      if (x->S == 0 || x->n_cases > 0) {
+        std::vector<double> zero(N, 0.0);
+        e2 = cudaMemcpyAsync(out, zero.data(), count * sizeof(double),
+                             out_on_device ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost, x->stream);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(x->stream);
+        return e2 == cudaSuccess ? LBM_OK : cuda_fail(x, e2, "current copy");
+      }
+      lbm::ReactArgs ra{x->mech, x->Xs[x->xs_cur], x->Xs[1 - x->xs_cur], x->rsrc};
+      if (x->precision == LBM_FP64) {
+        lbm::StepArgs<double> a{(const double*)x->pops[x->cur], nullptr, (const double*)x->phi,
+                                (const double*)x->Tfix, (double*)x->mac, x->status};
+        x->od.react_macro(x->pd, x->itd, a, ra, x->stream);
+      } else {
+        lbm::StepArgs<float> a{(const float*)x->pops[x->cur], nullptr, (const float*)x->phi,
+                               (const float*)x->Tfix, (float*)x->mac, x->status};
+        x->of.react_macro(x->pf, x->itf, a, ra, x->stream);
+      }
+      e2 = cudaGetLastError();
+      if (e2 == cudaSuccess)
+        e2 = cudaMemcpyAsync(out, x->rsrc + (size_t)(M + 1) * N, count * sizeof(double),
+                             out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, x->stream);
+      if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(x->stream);
+      return e2 == cudaSuccess ? LBM_OK : cuda_fail(x, e2, "current");
+    }
     case LBM_MOM_XS: {
       count = (size_t)x->S * N;
       if (bytes < count * sizeof(double)) return fail(x, LBM_ERR_ARG, "output buffer too small");

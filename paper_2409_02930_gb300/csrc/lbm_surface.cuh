@@ -9,10 +9,11 @@
 // the Jacobian is FP64 on the FP64 path and FP32 on the FP32 path, and is
 // reused across iterations (iterative refinement to the same FP64 root).  Then the gas mass production
 // (eq:totalFluidReactionRate, eq:molarToMassRates), the new coverages
-// (eq:surfaceMoleFractions, eq:totalSurfaceReactionRate without edges) and
-// the change of the fluid internal energy that keeps the unified internal
-// energy of fluid and adsorbed phases constant (eq:temperatureCell,
-// eq:InternalEnergyCell_PC; no electrochemical work or ohmic heat).
+// (eq:surfaceMoleFractions, eq:totalSurfaceReactionRate with the TPB edge
+// steps), the volumetric current (eq:volumetricCurrent) and the change of the
+// fluid internal energy: the unified internal energy of fluid and adsorbed
+// phases (eq:temperatureCell, eq:InternalEnergyCell_PC) gains the ohmic heat
+// and loses the electric power of the current (Sec. 4.2).
 #pragma once
 
 #include "lbm_compact.cuh"
@@ -46,7 +47,15 @@ struct MechDev {
   double T_thermo;
   double dt;                         // physical time step [s]
   double cvel2;                      // (dx/dt)^2 [m^2/s^2]
+  // electrochemistry: TPB (edge) steps run as surface steps whose extent is
+  // counted per unit surface (the per-length extent times l_tpb/a_s), so
+  // their constants carry the factor l_tpb/a_s and the potential factor
+  int edge[RMAX];
+  double nel[RMAX];                  // electrons released per step
+  double l_tpb, beta_ct, resist, dphi, dx;
 };
+
+constexpr double FARADAY_DEV = 96485.33212;   // C/mol
 
 // stoichiometric coefficient of species i in its q-th step, in the Jacobian's precision
 template <class RK> __device__ __forceinline__ RK sr_nu(const MechDev& mc, int i, int q);
@@ -73,13 +82,16 @@ __device__ __forceinline__ double ipow(double x, int n) {
 // converges to the same FP64 solution.
 template <int M, class RK>
 __device__ void surface_source_dev(const MechDev& mc, double T, const double* rho_a, double phi, const double* Xs0,
-                                   double* rhodot, double* Xs1, double& dU, int* status) {
+                                   double* rhodot, double* Xs1, double& dU, double& current, int* status) {
   const int S = mc.S, Rn = mc.R, NS = M + mc.S;
   double c0[MMAX + SMAX], kr[RMAX], xi[RMAX];
   for (int a = 0; a < M; ++a) c0[a] = rho_a[a] / mc.m[a];
   for (int s = 0; s < S; ++s) c0[M + s] = mc.gamma * Xs0[s];
   for (int k = 0; k < Rn; ++k) {
     kr[k] = mc.A[k] * exp(-mc.Ea[k] / (R_UNIV_DEV * T));
+    // TPB step: rate per unit TPB length, extent counted per unit surface
+    if (mc.edge[k])
+      kr[k] *= (mc.l_tpb / mc.a_s) * exp(mc.beta_ct * mc.nel[k] * FARADAY_DEV * mc.dphi / (R_UNIV_DEV * T));
     xi[k] = 0.0;
   }
   const double scale = mc.a_s / phi;     // gas concentration change per extent
@@ -209,7 +221,17 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
     const double Us = mc.Us0[s] + mc.cvs[s] * R_UNIV_DEV * (T - mc.T_thermo);
     dUs += mc.a_s * dn * Us;
   }
-  dU = -dUs / mc.cvel2;
+  // volumetric current: F a_s (electrons per unit surface) per second, the
+  // same as F l_tpb (electrons per TPB length) per second
+  double ne = 0.0;
+  for (int k = 0; k < Rn; ++k)
+    if (mc.edge[k]) ne += mc.nel[k] * xi[k];
+  current = FARADAY_DEV * mc.a_s * ne / mc.dt;
+  // ohmic heat stays in the fluid, electric power leaves (Sec. 4.2)
+  double Usrc = 0.0;
+  if (mc.l_tpb > 0.0)
+    Usrc = ((mc.a_s / mc.l_tpb) * current * current * mc.resist * mc.dx - fabs(mc.dphi) * current) * mc.dt;
+  dU = (-dUs + Usrc) / mc.cvel2;
 }
 
 // Arguments of the reactive passes.
@@ -217,7 +239,7 @@ struct ReactArgs {
   const MechDev* mech;
   const double* Xs_in;     // [S][N]
   double* Xs_out;          // [S][N]
-  double* src;             // [M + 1][N]: rhodot_a, then dU
+  double* src;             // [M + 2][N]: rhodot_a, then dU, then the volumetric current
 };
 
 // Pass 1: macro fields (as k_macro) plus the surface source of the node.
@@ -239,12 +261,13 @@ __global__ void __launch_bounds__(128) k_macro_react(Params<R> p, InletTables<R>
   State<R, D, M> s;
   s.template from_moments<EN, false>(p, mo, a.phi[n], EN ? R(0) : a.Tfix[n]);
   const MechDev& mc = *ra.mech;
-  double rho[MMAX], Xs0[SMAX], Xs1[SMAX], rd[MMAX], dU = 0.0;
+  double rho[MMAX], Xs0[SMAX], Xs1[SMAX], rd[MMAX], dU = 0.0, cur = 0.0;
   for (int k = 0; k < M; ++k) rho[k] = (double)s.rho_a[k];
   for (int k = 0; k < mc.S; ++k) Xs0[k] = ra.Xs_in[(size_t)k * p.N + n];
-  surface_source_dev<M, R>(mc, (double)s.T, rho, (double)s.phi, Xs0, rd, Xs1, dU, a.status);
+  surface_source_dev<M, R>(mc, (double)s.T, rho, (double)s.phi, Xs0, rd, Xs1, dU, cur, a.status);
   for (int k = 0; k < M; ++k) ra.src[(size_t)k * p.N + n] = rd[k];
   ra.src[(size_t)M * p.N + n] = dU;
+  ra.src[(size_t)(M + 1) * p.N + n] = cur;
   for (int k = 0; k < mc.S; ++k) ra.Xs_out[(size_t)k * p.N + n] = Xs1[k];
 }
 

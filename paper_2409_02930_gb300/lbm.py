@@ -19,7 +19,7 @@ LBM_OK, LBM_ERR_ARG, LBM_ERR_ALLOC, LBM_ERR_NUMERIC, LBM_ERR_TIMEOUT, LBM_ERR_ST
 LBM_BC = {"periodic": 0, "inlet": 1, "bounceback": 2}
 LBM_FP64, LBM_FP32 = 0, 1
 (LBM_MOM_RHO_A, LBM_MOM_J_A, LBM_MOM_RHO, LBM_MOM_U, LBM_MOM_T, LBM_MOM_P, LBM_MOM_V_A, LBM_MOM_N_A,
- LBM_MOM_XS, LBM_MOM_RHO_S) = range(10)
+ LBM_MOM_XS, LBM_MOM_RHO_S, LBM_MOM_CURRENT) = range(11)
 
 _dp = ctypes.POINTER(ctypes.c_double)
 
@@ -44,6 +44,9 @@ class LbmConfig(ctypes.Structure):
         ("gamma", ctypes.c_double), ("a_s", ctypes.c_double),
         ("surf_cv_factor", _dp), ("surf_U0", _dp), ("Xs_init", _dp),
         ("stream", ctypes.c_void_p),
+        ("edge", ctypes.POINTER(ctypes.c_int)), ("n_el", _dp),
+        ("l_tpb", ctypes.c_double), ("beta_ct", ctypes.c_double), ("resistivity", ctypes.c_double),
+        ("dphi", ctypes.c_double),
     ]
 
 
@@ -195,6 +198,13 @@ def make_config(wl, precision: int = LBM_FP64, stream=None, kappa_threshold: flo
         c.surf_cv_factor = arr(mech.surf_cv_factor)
         c.surf_U0 = arr(mech.surf_U0)
         c.Xs_init = arr(mech.Xs_init)
+        if getattr(mech, "edge", None) is not None:
+            e = np.ascontiguousarray(np.asarray(mech.edge, dtype=np.int32))
+            keep.append(e)
+            c.edge = e.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+            c.n_el = arr(mech.n_el)
+            c.l_tpb, c.beta_ct = mech.l_tpb, mech.beta_ct
+            c.resistivity, c.dphi = mech.resistivity, mech.dphi
     c.stream = stream if stream is not None else _current_stream()
     return c, keep
 
@@ -248,7 +258,7 @@ class Lattice:
         S = self.wl.mechanism.S if getattr(self.wl, "mechanism", None) is not None else 0
         return {LBM_MOM_RHO_A: (M, N), LBM_MOM_J_A: (M, D, N), LBM_MOM_RHO: (N,), LBM_MOM_U: (D, N),
                 LBM_MOM_T: (N,), LBM_MOM_P: (N,), LBM_MOM_V_A: (M, D, N), LBM_MOM_N_A: (M, D, N),
-                LBM_MOM_XS: (S, N), LBM_MOM_RHO_S: (N,)}[which]
+                LBM_MOM_XS: (S, N), LBM_MOM_RHO_S: (N,), LBM_MOM_CURRENT: (N,)}[which]
 
     def moments(self, which: int) -> np.ndarray:
         out = np.empty(self.moment_shape(which))

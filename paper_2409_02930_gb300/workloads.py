@@ -62,6 +62,13 @@ class Mechanism:
     elements_gas: np.ndarray     # (M, E) element counts of gas species
     elements_surf: np.ndarray    # (S, E) element counts of adsorbates
     Xs_init: np.ndarray          # (S,) initial coverages (uniform)
+    # electrochemistry (Sec. 4): steps on the triple-phase boundary (TPB edge)
+    edge: Optional[np.ndarray] = None     # (R,) 1 for a TPB step (rate per unit TPB length)
+    n_el: Optional[np.ndarray] = None     # (R,) electrons released by the step
+    l_tpb: float = 0.0                    # TPB length per volume of porous medium [1/m^2]
+    beta_ct: float = 0.5                  # charge-transfer symmetry factor
+    resistivity: float = 0.0              # electrolyte resistivity [Ohm m]
+    dphi: float = 0.0                     # Phi_electrode - Phi_electrolyte [V]
 
 
 @dataclasses.dataclass
@@ -405,7 +412,8 @@ def anode3d(nx=256, ny=128, nz=128, seed_phi=3, seed_X=4, steps=200, dx=0.25e-6,
 _ATOMIC_MASS = np.array([1.008e-3, 12.011e-3, 14.007e-3, 15.999e-3])
 
 
-def surface_mechanism(seed=4, gamma=2.6e-5, a_s=1.0e7) -> Mechanism:
+def surface_mechanism(seed=4, gamma=2.6e-5, a_s=1.0e7, electrochem=False, dphi=0.2, l_tpb=1.0e12,
+                      resistivity=0.3) -> Mechanism:
     """Seeded mass-action surface mechanism on one catalytic surface for the
     six-species gas (H2, H2O, CO, CO2, CH4, N2).
 
@@ -416,7 +424,17 @@ def surface_mechanism(seed=4, gamma=2.6e-5, a_s=1.0e7) -> Mechanism:
     log10 A uniform in [5, 15] (SI units of each step's order) and
     E_a uniform in [50, 150] kJ/mol.  Site density 2.6e-5 mol/m^2 and
     specific area a_s = 20 / delta_util with delta_util = 2 um (Sec. 5.2).
-    The prefactors are drawn in (mol, cm, s) units and stored in SI."""
+    The prefactors are drawn in (mol, cm, s) units and stored in SI.
+
+    With electrochem=True four charge-transfer steps on the triple-phase
+    boundary follow (Sec. 4: edge steps between adsorbates only, rates per
+    unit TPB length): H(s) + O(s) -> OH(s) + s + e and back, H(s) + OH(s) ->
+    H2O(s) + s + e and back, the oxide and hydroxide adsorbates standing in
+    for the ions of the electrolyte surface.  log10 A uniform in [7.5, 8.5]
+    (m^3 mol^-1 s^-1), E_a uniform in [70, 90] kJ/mol (own seeded stream),
+    TPB length l_tpb per volume of porous medium, potential difference dphi
+    = Phi_electrode - Phi_electrolyte, electrolyte resistivity, symmetry
+    factor 0.5."""
     gas = ["H2", "H2O", "CO", "CO2", "CH4", "N2"]
     surf = ["s", "H(s)", "O(s)", "OH(s)", "H2O(s)", "CO(s)", "C(s)", "CH(s)"]
     el_gas = np.array([[2, 0, 0, 0], [2, 0, 0, 1], [0, 1, 0, 1], [0, 1, 0, 2], [4, 1, 0, 0], [0, 0, 2, 0]])
@@ -465,13 +483,41 @@ def surface_mechanism(seed=4, gamma=2.6e-5, a_s=1.0e7) -> Mechanism:
     A = A_cgs * 1e4 * 1e-6 ** n_gas * 1e-4 ** n_surf
     Ea = rng.uniform(50.0e3, 150.0e3, R)
     ms = el_surf @ _ATOMIC_MASS
+    edge = n_el = None
+    if electrochem:
+        ct = [({"H(s)": -1, "O(s)": -1, "OH(s)": 1, "s": 1}, 1.0),
+              ({"OH(s)": -1, "s": -1, "H(s)": 1, "O(s)": 1}, -1.0),
+              ({"H(s)": -1, "OH(s)": -1, "H2O(s)": 1, "s": 1}, 1.0),
+              ({"H2O(s)": -1, "s": -1, "H(s)": 1, "OH(s)": 1}, -1.0)]
+        add_s = np.zeros((len(ct), S))
+        for k, (st, _) in enumerate(ct):
+            for name, v in st.items():
+                add_s[k, surf.index(name)] = v
+        assert np.all(add_s @ el_surf == 0) and np.all(add_s.sum(axis=1) == 0)
+        rng2 = np.random.default_rng(seed + 100)
+        nu_g = np.vstack([nu_g, np.zeros((len(ct), M))])
+        nu_s = np.vstack([nu_s, add_s])
+        A = np.concatenate([A, 10.0 ** rng2.uniform(7.5, 8.5, len(ct))])
+        Ea = np.concatenate([Ea, rng2.uniform(70.0e3, 90.0e3, len(ct))])
+        edge = np.concatenate([np.zeros(R, dtype=np.int32), np.ones(len(ct), dtype=np.int32)])
+        n_el = np.concatenate([np.zeros(R), [c[1] for c in ct]])
+        R = R + len(ct)
     Xs0 = np.array([0.9, 0.02, 0.02, 0.01, 0.02, 0.02, 0.005, 0.005])
     # molar C_v / R_U of the adsorbates, molecule-like; the empty site carries
     # no internal energy, so an adsorbing molecule takes its energy along
     cvs = np.array([0.0, 1.5, 1.5, 2.5, 3.0, 2.5, 1.5, 2.5])
     return Mechanism(S=S, R=R, nu_gas=nu_g, nu_surf=nu_s, A=A, Ea=Ea, gamma=gamma, a_s=a_s,
                      surf_molar_mass=ms, surf_cv_factor=cvs, surf_U0=np.zeros(S),
-                     gas_U0_molar=np.zeros(M), elements_gas=el_gas, elements_surf=el_surf, Xs_init=Xs0)
+                     gas_U0_molar=np.zeros(M), elements_gas=el_gas, elements_surf=el_surf, Xs_init=Xs0,
+                     edge=edge, n_el=n_el, l_tpb=l_tpb if electrochem else 0.0, beta_ct=0.5,
+                     resistivity=resistivity if electrochem else 0.0, dphi=dphi if electrochem else 0.0)
+
+
+def anode3d_electro(nx=256, ny=128, nz=128, steps=200, dphi=0.2, name=None) -> Workload:
+    """The 3-D anode with the seeded surface mechanism and its charge-transfer
+    steps on the triple-phase boundary at the potential difference dphi."""
+    return anode3d(nx=nx, ny=ny, nz=nz, steps=steps, mechanism=surface_mechanism(electrochem=True, dphi=dphi),
+                   name=name or f"anode3d_electro_{nx}x{ny}x{nz}")
 
 
 def anode3d_reactive(nx=256, ny=128, nz=128, steps=200, name=None) -> Workload:

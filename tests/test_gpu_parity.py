@@ -281,3 +281,57 @@ def test_fp32_reactive_matches_oracle(L):
     assert e < 1e-5, e
     xs_g, xs_o = g.moments(L.LBM_MOM_XS), o.moments(oracle.MOM_XS)
     assert np.max(np.abs(xs_g - xs_o)) < 1e-8
+
+
+def electro_3d(steps=20, nx=12, ny=8, nz=6, dphi=0.2):
+    return W.anode3d_electro(nx=nx, ny=ny, nz=nz, steps=steps, dphi=dphi,
+                             name=f"anode3d_electro_{nx}x{ny}x{nz}")
+
+
+@pytest.mark.parametrize("dphi", [0.0, 0.4])
+def test_fp64_electrochemistry_matches_oracle(L, dphi):
+    """The anode with charge-transfer steps on the triple-phase boundary
+    (Sec. 4): populations, moments, coverages and the volumetric current of
+    the FP64 GPU step match the oracle.  The GPU counts an edge step's extent
+    per unit surface (its constant times l_tpb/a_s) where the oracle counts it
+    per unit TPB length; the two must agree.  At these potentials the current
+    has opposite signs."""
+    wl = electro_3d(dphi=dphi)
+    o = oracle.Oracle(wl)
+    g = L.Lattice(wl, precision=L.LBM_FP64)
+    o.step(wl.steps)
+    g.step(wl.steps)
+    g.sync()
+    po, pg = o.pops(), g.populations()
+    for l in range(g.L):
+        assert field_err(pg[l], po[l]) < 1e-12, ("lattice", l)
+    for name in ("RHO_A", "RHO", "U", "T", "N_A"):
+        k = getattr(L, "LBM_MOM_" + name)
+        assert field_err(g.moments(k), o.moments(k)) < 1e-12, name
+    xs_g, xs_o = g.moments(L.LBM_MOM_XS), o.moments(oracle.MOM_XS)
+    assert np.max(np.abs(xs_g - xs_o)) < 1e-12
+    ig, io = g.moments(L.LBM_MOM_CURRENT), o.moments(oracle.MOM_CURRENT)
+    assert np.abs(io).max() > 1e6                      # A/m^3: the TPB steps run
+    assert field_err(ig, io) < 1e-11, field_err(ig, io)
+    assert np.sign(io.mean()) == (1.0 if dphi > 0.2 else -1.0)
+
+
+def test_fp32_electrochemistry_matches_oracle(L):
+    """FP32 populations with the FP64 surface source and the TPB steps:
+    densities within 1e-5 after 200 steps, coverages within 1e-8, the
+    volumetric current within 1e-4 of its largest value: the rate constants
+    carry exp(-E_a/(R_U T)) with E_a/(R_U T) near 9, so the FP32 temperature's
+    relative error (a few 1e-6) reaches the current about ten times larger
+    (measured 2.4e-5)."""
+    wl = electro_3d(steps=200)
+    o = oracle.Oracle(wl)
+    g = L.Lattice(wl, precision=L.LBM_FP32)
+    o.step(wl.steps)
+    g.step(wl.steps)
+    g.sync()
+    e = field_err(g.moments(L.LBM_MOM_RHO_A), o.moments(oracle.MOM_RHO_A))
+    assert e < 1e-5, e
+    xs_g, xs_o = g.moments(L.LBM_MOM_XS), o.moments(oracle.MOM_XS)
+    assert np.max(np.abs(xs_g - xs_o)) < 1e-8
+    ei = field_err(g.moments(L.LBM_MOM_CURRENT), o.moments(oracle.MOM_CURRENT))
+    assert ei < 1e-4, ei

@@ -106,10 +106,11 @@ T_RX, PHI_RX, A_S, GAMMA = 1000.0, 0.5, 1.0e7, 2.6e-5
 M_A, M_B = 28.0e-3, 40.0e-3
 
 
-def _uniform_reactive(nu_gas, nu_surf, A, Ea, Xs0, X_gas=(0.5, 0.5), nx=3, ny=3):
+def _uniform_reactive(nu_gas, nu_surf, A, Ea, Xs0, X_gas=(0.5, 0.5), nx=3, ny=3, energy=False, electro=None):
     """Uniform periodic 2-D lattice of gas A and an inert gas B at 1 atm and
-    1000 K (isothermal) over a surface with the given steps; every node is
-    the same well-mixed reactor."""
+    1000 K (isothermal unless energy) over a surface with the given steps;
+    every node is the same well-mixed reactor.  electro: (edge flags,
+    electrons per step, l_tpb, resistivity, dphi) for TPB steps."""
     N = nx * ny
     S = len(Xs0)
     R = len(A)
@@ -118,9 +119,13 @@ def _uniform_reactive(nu_gas, nu_surf, A, Ea, Xs0, X_gas=(0.5, 0.5), nx=3, ny=3)
                        surf_molar_mass=np.full(S, M_A), surf_cv_factor=np.zeros(S), surf_U0=np.zeros(S),
                        gas_U0_molar=np.zeros(2), elements_gas=np.eye(2, dtype=int),
                        elements_surf=np.zeros((S, 2), dtype=int), Xs_init=np.asarray(Xs0, float))
+    if electro is not None:
+        mech.edge, mech.n_el, mech.l_tpb, mech.resistivity, mech.dphi = electro
+        mech.edge = np.asarray(mech.edge, np.int32)
+        mech.n_el = np.asarray(mech.n_el, float)
     wl = W.Workload(
         name="uniform_reactor", nx=nx, ny=ny, nz=1, bc_lo=W.BC_PERIODIC, bc_hi=W.BC_PERIODIC, M=2,
-        energy=False, knudsen=False, dx=1.0e-6, theta_max=1.0 / 3.0, T_scale=T_RX, T_ref=T_RX, P_ref=W.ATM,
+        energy=energy, knudsen=False, dx=1.0e-6, theta_max=1.0 / 3.0, T_scale=T_RX, T_ref=T_RX, P_ref=W.ATM,
         molar_mass=np.array([M_A, M_B]), D_ref=np.array([[0.0, 2e-4], [2e-4, 0.0]]),
         mu_ref=np.array([4e-5, 4e-5]), mu_exp=0.7, Pr=0.7, bulk_ratio=1.0, cv_factor=np.array([2.5, 1.5]),
         U0=np.zeros(2), T_thermo=0.0, tortuosity=1.0, pore_radius=1e-6, porosity=np.full(N, PHI_RX),
@@ -210,3 +215,67 @@ def test_reversible_adsorption_reaches_its_equilibrium():
     np.testing.assert_allclose(Xs[1], thA[0] / GAMMA, rtol=1e-10)
     cA = o.moments(oracle.MOM_RHO_A)[0] / M_A
     np.testing.assert_allclose(kf * cA * Xs[0] * GAMMA, kb * Xs[1] * GAMMA, rtol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# electrochemistry (Sec. 4): charge-transfer steps on the triple-phase boundary
+# ---------------------------------------------------------------------------
+F_C = 96485.33212
+L_TPB, OHM = 1.0e12, 0.3
+
+
+@pytest.mark.parametrize("dphi", [0.0, 0.15])
+def test_tpb_step_extent_current_and_potential(dphi):
+    """H(s) + O(s) -> OH(s) + s + e on the TPB edge (rate per unit TPB
+    length r = k theta_H theta_O, k = A exp(-Ea/RT) exp(beta n F dphi/RT),
+    reading R29).  Its extent xi [mol/m] changes the surface concentrations
+    by lambda xi, lambda = l_TPB/a^(s) (eq:totalSurfaceReactionRate), so one
+    backward-Euler step solves xi = dt k (thH - lambda xi)(thO - lambda xi);
+    the coverage of OH(s) grows by lambda xi/Gamma and the volumetric current
+    is I = F l_TPB xi/dt (eq:volumetricCurrent)."""
+    nu_s = [[1, -1, -1, 1]]                  # s, H(s), O(s), OH(s): H + O -> OH + s
+    X0 = [0.7, 0.1, 0.15, 0.05]
+    probe = oracle.Oracle(_uniform_reactive([[0, 0]], nu_s, [1.0], [0.0], X0,
+                                            electro=([1], [1.0], L_TPB, OHM, dphi)))
+    dt = probe.dt
+    lam = L_TPB / A_S
+    thH, thO = 0.1 * GAMMA, 0.15 * GAMMA
+    A, Ea = _rate_constant_for(dt, 0.5 / (lam * (thH + thO)))
+    wl = _uniform_reactive([[0, 0]], nu_s, [A], [Ea], X0, electro=([1], [1.0], L_TPB, OHM, dphi))
+    o = oracle.Oracle(wl)
+    I_seen = o.moments(oracle.MOM_CURRENT)
+    o.step(1)
+    k = A * np.exp(-Ea / (R_U * T_RX)) * np.exp(0.5 * 1.0 * F_C * dphi / (R_U * T_RX))
+    a2, a1, a0 = dt * k * lam * lam, -(1.0 + dt * k * lam * (thH + thO)), dt * k * thH * thO
+    xi = (-a1 - np.sqrt(a1 * a1 - 4 * a2 * a0)) / (2 * a2)
+    Xs = o.moments(oracle.MOM_XS)
+    np.testing.assert_allclose(Xs[3], 0.05 + lam * xi / GAMMA, rtol=1e-12)
+    np.testing.assert_allclose(Xs[1], 0.1 - lam * xi / GAMMA, rtol=1e-12)
+    np.testing.assert_allclose(I_seen, F_C * L_TPB * xi / dt, rtol=1e-12)
+
+
+def test_tpb_energy_source_is_ohmic_heat_minus_electric_work():
+    """With the energy lattice on, a uniform reactor's fluid energy changes
+    over one step by the adsorbed phase's loss plus (P_Omega - P_elec) dt,
+    P_elec = |dphi| I, P_Omega = (a^(s)/l_TPB) I^2 Omega dx (Sec. 4.2,
+    reading R28).  The adsorbates here carry no internal energy, so the
+    change is the electrochemical source alone; its sign follows the
+    current."""
+    nu_s = [[1, -1, -1, 1]]
+    X0 = [0.7, 0.1, 0.15, 0.05]
+    dphi = 0.15
+    probe = oracle.Oracle(_uniform_reactive([[0, 0]], nu_s, [1.0], [0.0], X0, energy=True,
+                                            electro=([1], [1.0], L_TPB, OHM, dphi)))
+    A, Ea = _rate_constant_for(probe.dt, 0.01 / (L_TPB / A_S * 0.25 * GAMMA))
+    wl = _uniform_reactive([[0, 0]], nu_s, [A], [Ea], X0, energy=True, electro=([1], [1.0], L_TPB, OHM, dphi))
+    o = oracle.Oracle(wl)
+    I = o.moments(oracle.MOM_CURRENT)
+    o.step(1)
+    pre, post = o.pulled(), o.pops()
+    M = wl.M
+    dE = (post[M + 1].sum(0) - pre[M + 1].sum(0)) * o.cvel ** 2      # J per m^3 of medium
+    P_elec = abs(dphi) * I
+    P_ohm = (A_S / L_TPB) * I * I * OHM * wl.dx
+    expect = (P_ohm - P_elec) * o.dt
+    assert np.all(np.abs(expect) > 0)
+    np.testing.assert_allclose(dE, expect, rtol=1e-9)

@@ -260,6 +260,17 @@ int lbm_step_host(lbm_ctx* ctx, const void* in_host, void* out_host, int n_steps
 int lbm_sync(lbm_ctx* ctx);
 
 /*
+ * lbm_set_potential -- the potential difference Phi_electrode -
+ * Phi_electrolyte [V] seen by the TPB steps (Sec. 4, Sec. 4.1): field is a
+ * host array of N values, one per node, or NULL for `uniform` everywhere.
+ * The electrode phase has one potential (eq:electrodePotential) while the
+ * electrolyte potential varies along the cell (eq:electrolytePotential), so a
+ * driver of the membrane-electrode assembly sets the field between steps.
+ * Synchronous.  Errors: LBM_ERR_STATE (no surface mechanism), LBM_ERR_ALLOC.
+ */
+int lbm_set_potential(lbm_ctx* ctx, const double* field, double uniform);
+
+/*
  * lbm_set_wait_limit -- the bound of the device waits of the kernel forms
  * that stage lattice rows with bulk tensor copies: the number of mbarrier
  * probes a wait makes before it gives up (default 4194304).  The paper has

@@ -103,6 +103,7 @@ def _declare(L):
     L.oc_moments.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
     L.oc_moments_lane.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp]
     L.oc_set_tangents.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+    L.oc_set_potential.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double]
     L.oc_threads.restype = ctypes.c_int
     L.oc_lanes.restype = ctypes.c_int
     L.oc_product_form.argtypes = [ctypes.c_int, _dp, _dp, _dp]
@@ -226,6 +227,16 @@ class Oracle:
         if h is not None:
             self._L.oc_destroy(h)
             self._h = None
+
+    def set_potential(self, field=None, uniform: float = 0.0):
+        """Phi_electrode - Phi_electrolyte of the TPB steps [V]: a field of N
+        values, or `uniform` everywhere when field is None."""
+        if field is None:
+            self._L.oc_set_potential(self._h, None, float(uniform))
+        else:
+            f = _f64(field).reshape(-1)
+            assert f.size == self.N
+            self._L.oc_set_potential(self._h, _ptr(f), float(uniform))
 
     def step(self, n: int = 1):
         self._L.oc_step(self._h, int(n))

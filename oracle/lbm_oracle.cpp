@@ -351,6 +351,7 @@ struct Oracle {
   real gamma, a_s, ms[SMAX], cvs[SMAX], Us0[SMAX], Ug0[MMAX];
   int edge[RMAX];
   double nel[RMAX], l_tpb, beta_ct, resist, dphi;
+  std::vector<double> dphi_node;      // per-node Phi_electrode - Phi_electrolyte (empty: dphi everywhere)
   // state
   std::vector<real> pops, pulled, phi, Tfix, Xs, Xs_new;
   std::vector<Macro> mac;
@@ -466,7 +467,7 @@ void compute_macro(const Oracle& o, const real* fpop /* [nl][Q] */, real phi, re
 // eq:totalFluidReactionRate / eq:molarToMassRates) and the new coverages.
 // ---------------------------------------------------------------------------
 void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhodot_f,
-                    real* Xs1, real& dU_fluid_volumetric, real& current);
+                    real* Xs1, real& dU_fluid_volumetric, real& current, double dphi);
 
 // ---------------------------------------------------------------------------
 // One node's collision (a4 .. a9).  fin: streamed populations [nl][Q];
@@ -553,7 +554,9 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   for (int a = 0; a < M; ++a) rhodot[a] = 0.0;
   real dU_src = 0.0;
   real Iv = 0.0;
-  if (o.S > 0) surface_source(o, m, Xs0, rhodot, Xs1, dU_src, Iv);
+  // potential difference Phi_electrode - Phi_electrolyte at this node
+  const double dphi_n = o.dphi_node.empty() ? o.dphi : o.dphi_node[n];
+  if (o.S > 0) surface_source(o, m, Xs0, rhodot, Xs1, dU_src, Iv, dphi_n);
   const_cast<Oracle&>(o).dg_current[n] = Iv;
   for (int a = 0; a < M; ++a) const_cast<Oracle&>(o).dg_rhodot[(size_t)a * o.N + n] = rhodot[a];
 
@@ -823,10 +826,10 @@ void gradients(const Oracle& o, int n, Grad& gr) {
 // (charge transfer with symmetry factor beta; reading R29).
 const double FARADAY = 96485.33212;     // C/mol
 
-void mass_action_rates(const Oracle& o, real T, const real* cg, const real* cs, real* r) {
+void mass_action_rates(const Oracle& o, real T, const real* cg, const real* cs, real* r, double dphi) {
   for (int k = 0; k < o.Rn; ++k) {
     real kr = o.Apre[k] * r_exp(-o.Ea[k] / (R_UNIV * T));
-    if (o.edge[k]) kr *= r_exp(o.beta_ct * o.nel[k] * FARADAY * o.dphi / (R_UNIV * T));
+    if (o.edge[k]) kr *= r_exp(o.beta_ct * o.nel[k] * FARADAY * dphi / (R_UNIV * T));
     real v = kr;
     for (int a = 0; a < o.M; ++a)
       if (o.nu_g[k][a] < 0) v *= r_pow(rmax(cg[a], 0.0), -o.nu_g[k][a]);
@@ -840,7 +843,7 @@ void mass_action_rates(const Oracle& o, real T, const real* cg, const real* cs, 
 // xi = dt * r(c_gas0 + (a_s/phi) nu_g^T xi, theta0 + nu_s^T xi), solved by
 // Newton with a finite-difference-free analytic Jacobian of mass action.
 void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhodot_f,
-                    real* Xs1, real& dU_fluid_volumetric, real& current) {
+                    real* Xs1, real& dU_fluid_volumetric, real& current, double dphi) {
   const int M = o.M, S = o.S, Rn = o.Rn;
   const real T = m.T;
   const real dtp = o.dt;                        // physical seconds
@@ -859,7 +862,7 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
     for (int a = 0; a < M; ++a) { cg[a] = cg0[a]; for (int k = 0; k < Rn; ++k) cg[a] += scale * o.nu_g[k][a] * xi[k]; }
     for (int s = 0; s < S; ++s) { cs[s] = cs0[s]; for (int k = 0; k < Rn; ++k) cs[s] += o.nu_s[k][s] * es[k] * xi[k]; }
     real r[RMAX];
-    mass_action_rates(o, T, cg, cs, r);
+    mass_action_rates(o, T, cg, cs, r, dphi);
     real Fv[RMAX], J[RMAX * RMAX];
     for (int k = 0; k < Rn; ++k) Fv[k] = xi[k] - dtp * r[k];
     // Jacobian: dF_k/dxi_l = delta_kl - dt * dr_k/dxi_l
@@ -948,7 +951,7 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
   // source over the step (P_Omega - P_elec) dt
   real U_source = 0.0;
   if (o.l_tpb > 0.0) {
-    const real P_elec = std::fabs(o.dphi) * current;
+    const real P_elec = std::fabs(dphi) * current;
     const real P_ohm = (o.a_s / o.l_tpb) * current * current * o.resist * o.cfg.dx;
     U_source = (P_ohm - P_elec) * dtp;
   }
@@ -1255,6 +1258,15 @@ void oc_moments_lane(void* h, int which, int lane, double* out) { moments_lane((
 // dpore [lanes] and dtort [lanes] (null: zero) are the directions of the
 // porosity field, pore radius [m] and tortuosity; the populations are reset
 // to the initial equilibria, whose derivatives follow from the porosity.
+// Potential difference Phi_electrode - Phi_electrolyte of the TPB steps: per
+// node (field of N values) or, with field == NULL, the same everywhere.
+void oc_set_potential(void* h, const double* field, double uniform) {
+  Oracle* o = (Oracle*)h;
+  o->dphi = uniform;
+  if (field) o->dphi_node.assign(field, field + o->N);
+  else o->dphi_node.clear();
+}
+
 void oc_set_tangents(void* h, const double* dphi, const double* dpore, const double* dtort) {
   Oracle* o = (Oracle*)h;
 #ifdef ORACLE_DUAL

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -1123,6 +1124,26 @@ int lbm_set_wait_limit(lbm_ctx* x, int probes) {
   return LBM_OK;
 }
 
+int lbm_set_potential(lbm_ctx* x, const double* field, double uniform) {
+  if (!x) return LBM_ERR_ARG;
+  if (x->S == 0 || x->n_cases > 0) return fail(x, LBM_ERR_STATE, "no surface mechanism");
+  cudaError_t e = cudaSuccess;
+  const double* dev = nullptr;
+  if (field) {
+    if (!x->dphi_dev) e = cudaMalloc(&x->dphi_dev, (size_t)x->N * sizeof(double));
+    if (e != cudaSuccess) return fail(x, LBM_ERR_ALLOC, "potential field allocation failed");
+    e = cudaMemcpyAsync(x->dphi_dev, field, (size_t)x->N * sizeof(double), cudaMemcpyHostToDevice, x->stream);
+    dev = x->dphi_dev;
+  }
+  char* m = reinterpret_cast<char*>(x->mech);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m + offsetof(lbm::MechDev, dphi), &uniform, sizeof(double), cudaMemcpyHostToDevice, x->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m + offsetof(lbm::MechDev, dphi_field), &dev, sizeof(dev), cudaMemcpyHostToDevice, x->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  return e == cudaSuccess ? LBM_OK : cuda_fail(x, e, "potential upload");
+}
+
 int lbm_sync(lbm_ctx* x) {
   if (!x) return LBM_ERR_ARG;
   if (x->h2d) {
@@ -1164,8 +1185,9 @@ void lbm_destroy(lbm_ctx* x) {
   if (!x) return;
   cudaStreamSynchronize(x->stream);
   release_streaming(x);
-  void* bufs[15] = {x->pops[0], x->pops[1], x->phi, x->Tfix, x->mac, x->status, x->scratch_out,
-                   x->Xs[0], x->Xs[1], x->rsrc, x->mech, x->init_X, x->init_T, x->init_P, x->init_U};
+  void* bufs[16] = {x->pops[0], x->pops[1], x->phi, x->Tfix, x->mac, x->status, x->scratch_out,
+                   x->Xs[0], x->Xs[1], x->rsrc, x->mech, x->init_X, x->init_T, x->init_P, x->init_U,
+                   x->dphi_dev};
   for (void* b : bufs)
     if (b) cudaFree(b);
   drop_graphs(x);

@@ -50,6 +50,7 @@ struct lbm_ctx {
   double* Xs[2];
   int xs_cur;
   double* rsrc;
+  double* dphi_dev;                  // per-node potential difference of the TPB steps (lbm_set_potential)
   lbm::MechDev* mech;
   // initial fields kept on the device (lbm_adjoint restarts from them)
   double* init_X;                    // [M][N]

@@ -53,6 +53,7 @@ struct MechDev {
   int edge[RMAX];
   double nel[RMAX];                  // electrons released per step
   double l_tpb, beta_ct, resist, dphi, dx;
+  const double* dphi_field;          // per-node potential difference [N] (null: dphi everywhere)
 };
 
 constexpr double FARADAY_DEV = 96485.33212;   // C/mol
@@ -82,7 +83,8 @@ __device__ __forceinline__ double ipow(double x, int n) {
 // converges to the same FP64 solution.
 template <int M, class RK>
 __device__ void surface_source_dev(const MechDev& mc, double T, const double* rho_a, double phi, const double* Xs0,
-                                   double* rhodot, double* Xs1, double& dU, double& current, int* status) {
+                                   double* rhodot, double* Xs1, double& dU, double& current, double dphi,
+                                   int* status) {
   const int S = mc.S, Rn = mc.R, NS = M + mc.S;
   double c0[MMAX + SMAX], kr[RMAX], xi[RMAX];
   for (int a = 0; a < M; ++a) c0[a] = rho_a[a] / mc.m[a];
@@ -91,7 +93,7 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
     kr[k] = mc.A[k] * exp(-mc.Ea[k] / (R_UNIV_DEV * T));
     // TPB step: rate per unit TPB length, extent counted per unit surface
     if (mc.edge[k])
-      kr[k] *= (mc.l_tpb / mc.a_s) * exp(mc.beta_ct * mc.nel[k] * FARADAY_DEV * mc.dphi / (R_UNIV_DEV * T));
+      kr[k] *= (mc.l_tpb / mc.a_s) * exp(mc.beta_ct * mc.nel[k] * FARADAY_DEV * dphi / (R_UNIV_DEV * T));
     xi[k] = 0.0;
   }
   const double scale = mc.a_s / phi;     // gas concentration change per extent
@@ -230,7 +232,7 @@ __device__ void surface_source_dev(const MechDev& mc, double T, const double* rh
   // ohmic heat stays in the fluid, electric power leaves (Sec. 4.2)
   double Usrc = 0.0;
   if (mc.l_tpb > 0.0)
-    Usrc = ((mc.a_s / mc.l_tpb) * current * current * mc.resist * mc.dx - fabs(mc.dphi) * current) * mc.dt;
+    Usrc = ((mc.a_s / mc.l_tpb) * current * current * mc.resist * mc.dx - fabs(dphi) * current) * mc.dt;
   dU = (-dUs + Usrc) / mc.cvel2;
 }
 
@@ -264,7 +266,8 @@ __global__ void __launch_bounds__(128) k_macro_react(Params<R> p, InletTables<R>
   double rho[MMAX], Xs0[SMAX], Xs1[SMAX], rd[MMAX], dU = 0.0, cur = 0.0;
   for (int k = 0; k < M; ++k) rho[k] = (double)s.rho_a[k];
   for (int k = 0; k < mc.S; ++k) Xs0[k] = ra.Xs_in[(size_t)k * p.N + n];
-  surface_source_dev<M, R>(mc, (double)s.T, rho, (double)s.phi, Xs0, rd, Xs1, dU, cur, a.status);
+  const double dphi_n = mc.dphi_field ? mc.dphi_field[n] : mc.dphi;
+  surface_source_dev<M, R>(mc, (double)s.T, rho, (double)s.phi, Xs0, rd, Xs1, dU, cur, dphi_n, a.status);
   for (int k = 0; k < M; ++k) ra.src[(size_t)k * p.N + n] = rd[k];
   ra.src[(size_t)M * p.N + n] = dU;
   ra.src[(size_t)(M + 1) * p.N + n] = cur;

@@ -121,6 +121,8 @@ def load(path: str = LIB_PATH):
     L.lbm_save.restype = ctypes.c_int
     L.lbm_load.argtypes = [vp, vp, ctypes.c_size_t]
     L.lbm_load.restype = ctypes.c_int
+    L.lbm_set_potential.argtypes = [vp, _dp, ctypes.c_double]
+    L.lbm_set_potential.restype = ctypes.c_int
     L.lbm_set_wait_limit.argtypes = [vp, ctypes.c_int]
     L.lbm_set_wait_limit.restype = ctypes.c_int
     _lib = L
@@ -280,6 +282,21 @@ class Lattice:
 
     def variant(self) -> int:
         return int(load().lbm_get_variant(self._h))
+
+    def set_potential(self, field=None, uniform: float = 0.0):
+        """Phi_electrode - Phi_electrolyte of the TPB steps [V] (lbm_set_potential):
+        a field of N values, or `uniform` everywhere when field is None."""
+        if field is None:
+            self._check(load().lbm_set_potential(self._h, None, float(uniform)), "lbm_set_potential")
+        else:
+            f = _f64(field)
+            assert f.size == self.N
+            self._check(load().lbm_set_potential(self._h, f.ctypes.data_as(_dp), float(uniform)),
+                        "lbm_set_potential")
+
+    def current(self) -> np.ndarray:
+        """Volumetric current of the TPB steps per node [A/m^3] (LBM_MOM_CURRENT)."""
+        return self.moments(LBM_MOM_CURRENT)
 
     def set_wait_limit(self, probes: int):
         """Bound of the row-staged forms' device waits (lbm_set_wait_limit)."""

@@ -26,8 +26,12 @@ def test_traffic_table_entries_parse():
     assert "slab512x512_fp32_variant8" in keys
     for k in keys:
         t = bench.profiled_traffic(k)
-        # DRAM bytes per launch of the 95.4 MB (algorithmic) slab step
-        assert t is not None and 10e6 < t < 200e6, (k, t)
+        # DRAM bytes per launch against the algorithmic bytes of that lattice
+        # (364 per node): at most 2x, and no less than the 47 MB the 512^2
+        # step's reads alone need
+        side = int(k.split("x")[0].replace("slab", ""))
+        alg = 364 * side * side
+        assert t is not None and 0.45 * alg < t < 2.0 * alg, (k, t, alg)
     assert bench.profiled_traffic("slab512x512_fp32_variant_unknown") is None
 
 

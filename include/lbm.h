@@ -5,14 +5,14 @@
  * reactive mixtures in porous media", arXiv 2409.02930).
  *
  * One call of lbm_step advances every node by one fused stream-and-collide
- * time step: the M species lattices (Sec. 2.3, eqn:finalNumericalEquationsReactive
- * with the dusty-gas relaxation eqn:fStar and the diffusion-velocity system
- * eqn:transform1), the mixture momentum lattice (Sec. 3.2, eqn:f with the
- * extended equilibrium eq:feqmix and the net Knudsen force
- * eqn:netKnudsenForce), the mixture energy lattice (Sec. 3.3, eqn:g with
- * eq:geq_i and eq:gstar) and, when a surface mechanism is given, the
- * heterogeneous-reaction sources of Sec. 4.2 (eq:rho_pc, eqn:f_source,
- * eqn:g_source, eq:fsourceHetero).
+ * time step: the M species lattices (Sec. 2.3, Eq. 21
+ * with the dusty-gas relaxation Eq. 25 and the diffusion-velocity system
+ * Eq. 29), the mixture momentum lattice (Sec. 3.2, Eq. 42 with the
+ * extended equilibrium Eq. 44 and the net Knudsen force
+ * Eq. 48), the mixture energy lattice (Sec. 3.3, Eq. 43 with
+ * Eq. 51 and Eq. 54) and, when a surface mechanism is given, the
+ * heterogeneous-reaction sources of Sec. 4.2 (Eq. 78, Eq. 87,
+ * Eq. 88, Eq. 89).
  *
  * Conventions
  *   - All functions return LBM_OK (0) or a negative status code; no C++
@@ -61,18 +61,18 @@ extern "C" {
                                  exceeds kappa_threshold */
 
 /* moment selectors for lbm_moments (layout [component][n]) */
-#define LBM_MOM_RHO_A 0       /* species densities rho_a, [M][N], kg/m^3 (eq:density1) */
-#define LBM_MOM_J_A   1       /* species momenta sum_i f_ai c_i, [M][D][N], lattice units (eq:momentum1) */
-#define LBM_MOM_RHO   2       /* mixture density of the momentum lattice, [N], kg/m^3 (eqn:fdensity) */
-#define LBM_MOM_U     3       /* mixture velocity, [D][N], lattice units (eqn:f1momMomentum) */
-#define LBM_MOM_T     4       /* temperature, [N], K (eq:temperature) */
-#define LBM_MOM_P     5       /* pressure, [N], Pa (eqn:eosIdealGas) */
-#define LBM_MOM_V_A   6       /* diffusion velocities V_a, [M][D][N], lattice units (eqn:transform1) */
+#define LBM_MOM_RHO_A 0       /* species densities rho_a, [M][N], kg/m^3 (Eq. 4) */
+#define LBM_MOM_J_A   1       /* species momenta sum_i f_ai c_i, [M][D][N], lattice units (Eq. 5) */
+#define LBM_MOM_RHO   2       /* mixture density of the momentum lattice, [N], kg/m^3 (Eq. 37) */
+#define LBM_MOM_U     3       /* mixture velocity, [D][N], lattice units (Eq. 38) */
+#define LBM_MOM_T     4       /* temperature, [N], K (Eq. 41) */
+#define LBM_MOM_P     5       /* pressure, [N], Pa (Eq. 3) */
+#define LBM_MOM_V_A   6       /* diffusion velocities V_a, [M][D][N], lattice units (Eq. 29) */
 #define LBM_MOM_N_A   7       /* molar fluxes rho_a (u + V_a)/m_a, [M][D][N], mol m^-2 s^-1 */
-#define LBM_MOM_XS    8       /* surface coverages X^(s), [S][N] (eq:surfaceMoleFractions) */
-#define LBM_MOM_RHO_S 9       /* sum_a rho_a, [N], kg/m^3 (eq:rhoSpec) */
+#define LBM_MOM_XS    8       /* surface coverages X^(s), [S][N] (Eq. 70) */
+#define LBM_MOM_RHO_S 9       /* sum_a rho_a, [N], kg/m^3 (Eq. 1) */
 #define LBM_MOM_CURRENT 10    /* volumetric current of the TPB steps, [N], A per m^3 of porous medium
-                                 (eq:volumetricCurrent; zero without edge steps) */
+                                 (Eq. 74; zero without edge steps) */
 
 typedef struct lbm_ctx lbm_ctx;
 
@@ -128,10 +128,10 @@ typedef struct lbm_config {
   /* electrochemistry (Sec. 4): steps on the triple-phase boundary (TPB), an
    * edge whose length per volume of porous medium is l_tpb.  An edge step's
    * rate is per unit TPB length, involves adsorbates only, changes the
-   * coverages by nu l_tpb/(a_s Gamma) per extent (eq:totalSurfaceReactionRate)
+   * coverages by nu l_tpb/(a_s Gamma) per extent (Eq. 71)
    * and releases n_el electrons; its constant carries the factor
    * exp(beta_ct n_el F dphi/(R_U T)).  The volumetric current is
-   * F l_tpb (electrons per TPB length and second) (eq:volumetricCurrent); the
+   * F l_tpb (electrons per TPB length and second) (Eq. 74); the
    * fluid energy gains the ohmic heat (a_s/l_tpb) I^2 resistivity dx and
    * loses the electric power |dphi| I (Sec. 4.2).  edge == NULL: no edge
    * steps (the fields below are then not read). */
@@ -145,8 +145,8 @@ typedef struct lbm_config {
 
 /*
  * lbm_create -- validate cfg, allocate device state and set every population
- * to the equilibrium of the initial fields (eq:27eq, eq:feqmix without
- * extension, eq:geq_i).  On success *out holds a new context.
+ * to the equilibrium of the initial fields (Eq. 15, Eq. 44 without
+ * extension, Eq. 51).  On success *out holds a new context.
  * Errors: LBM_ERR_ARG (dimensions < 1, inlet face with nx < 3, M outside
  * {2, 3, 6}, porosity outside (0, 1], non-positive mass, temperature, pressure,
  * dx or theta_max), LBM_ERR_ALLOC, LBM_ERR_CUDA (no device).
@@ -263,8 +263,8 @@ int lbm_sync(lbm_ctx* ctx);
  * lbm_set_potential -- the potential difference Phi_electrode -
  * Phi_electrolyte [V] seen by the TPB steps (Sec. 4, Sec. 4.1): field is a
  * host array of N values, one per node, or NULL for `uniform` everywhere.
- * The electrode phase has one potential (eq:electrodePotential) while the
- * electrolyte potential varies along the cell (eq:electrolytePotential), so a
+ * The electrode phase has one potential (Eq. 75) while the
+ * electrolyte potential varies along the cell (Eq. 77), so a
  * driver of the membrane-electrode assembly sets the field between steps.
  * Synchronous.  Errors: LBM_ERR_STATE (no surface mechanism), LBM_ERR_ALLOC.
  */

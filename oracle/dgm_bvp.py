@@ -1,5 +1,5 @@
 """Steady dusty-gas transport through an open capillary: the boundary-value
-problem the lattice Boltzmann capillary relaxes to (Sec. 5.1, eq:constit2).
+problem the lattice Boltzmann capillary relaxes to (Sec. 5.1, Eq. 20).
 
 Test infrastructure, like the rest of oracle/: only tests may use it.
 
@@ -105,7 +105,7 @@ def profile(N, p0, L, D0, Dk, T, x):
 
 
 def binary_closed_form(XA0, XAL, L, DAB, DkA, mA, mB, c) -> float:
-    """Integrated binary eq:constit2 (isobaric, Graham's law): N_A =
+    """Integrated binary Eq. 20 (isobaric, Graham's law): N_A =
     c D_AB/(alpha L) ln[(1 - alpha X_A(L) + r)/(1 - alpha X_A(0) + r)],
     alpha = 1 - sqrt(m_A/m_B), r = D_AB / D^k_A."""
     alpha = 1.0 - np.sqrt(mA / mB)

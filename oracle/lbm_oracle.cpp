@@ -115,7 +115,7 @@ const int SMAX = 12;
 const int RMAX = 32;
 
 // ---------------------------------------------------------------------------
-// velocity set (Sec. 2.2, eq:d3q27vel): c_i in {-1,0,1}^D, D = 2 or 3.
+// velocity set (Sec. 2.2, Eq. 10): c_i in {-1,0,1}^D, D = 2 or 3.
 // ordering i = (cx+1) + 3 (cy+1) + 9 (cz+1).
 // ---------------------------------------------------------------------------
 struct Lattice {
@@ -140,7 +140,7 @@ Lattice make_lattice(int D) {
 }
 
 // ---------------------------------------------------------------------------
-// Product form, Sec. 2.2: eqn:phi0, eqn:phiPlus, eqn:phis and eq:prod.
+// Product form, Sec. 2.2: Eq. 11, Eq. 12, Eq. 13 and Eq. 14.
 // ---------------------------------------------------------------------------
 real psi(int c, real xi, real P) {
   if (c == 0) return 1.0 - P;
@@ -167,14 +167,14 @@ double lattice_weight(const Lattice& L, int i) {
 
 // ---------------------------------------------------------------------------
 // Polynomials in one velocity component w, used to apply the operators
-// O_alpha of eqn:oalpha literally (Sec. 3.3).
+// O_alpha of Eq. 50 literally (Sec. 3.3).
 // ---------------------------------------------------------------------------
 const int PDEG = 10;
 struct Poly { real a[PDEG + 1]; };
 
 Poly poly_zero() { Poly p; for (int k = 0; k <= PDEG; ++k) p.a[k] = 0.0; return p; }
 
-// O A = RT dA/dw + w A   (eqn:oalpha; reading R4: w = u/phi)
+// O A = RT dA/dw + w A   (Eq. 50; reading R4: w = u/phi)
 Poly poly_apply_O(const Poly& A, real RT) {
   Poly r = poly_zero();
   for (int k = 1; k <= PDEG; ++k) r.a[k - 1] += RT * k * A.a[k];
@@ -189,8 +189,8 @@ real poly_eval(const Poly& p, real w) {
 }
 
 // Psi_c(O, O^2) applied to the one-axis function h(w), evaluated at w:
-// c = 0: h - O^2 h ; c = +-1: (+-O h + O^2 h)/2  (eqn:phi0..eqn:phis with
-// xi -> O and P -> O^2, as eq:geq_i prescribes).
+// c = 0: h - O^2 h ; c = +-1: (+-O h + O^2 h)/2  (Eq. 11..Eq. 13 with
+// xi -> O and P -> O^2, as Eq. 51 prescribes).
 real psi_operator(int c, const Poly& h, real RT, real w) {
   Poly o1 = poly_apply_O(h, RT);
   Poly o2 = poly_apply_O(o1, RT);
@@ -200,8 +200,8 @@ real psi_operator(int c, const Poly& h, real RT, real w) {
   return 0.5 * (-v1 + v2);
 }
 
-// g^eq_i = phi rho Prod_alpha Psi_{c_i alpha}(O_alpha, O_alpha^2) E   (eq:geq_i)
-// with the generating function E = U + sum_beta w_beta^2 / 2 (eq:totalE),
+// g^eq_i = phi rho Prod_alpha Psi_{c_i alpha}(O_alpha, O_alpha^2) E   (Eq. 51)
+// with the generating function E = U + sum_beta w_beta^2 / 2 (Eq. 40),
 // w = u/phi (reading R4).  E is a sum of separable terms (a constant and one
 // quadratic per axis); the product of one-axis operators acts on each term
 // axis by axis.
@@ -229,7 +229,7 @@ void energy_equilibrium(const Lattice& L, real phi, real rho, const real* u, rea
 
 // ---------------------------------------------------------------------------
 // Householder QR solve of a small dense system, as the paper does for the
-// diffusion-velocity system (Sec. 2.3, after eqn:transform1Alternate).
+// diffusion-velocity system (Sec. 2.3, after Eq. 30).
 // A is n x n row-major, b has nrhs columns (b[k*nrhs + r]).
 // ---------------------------------------------------------------------------
 void householder_qr_solve(int n, const real* Ain, int nrhs, const real* bin, real* x) {
@@ -326,12 +326,12 @@ namespace {
 // Per-node macroscopic state of the streamed populations (Sec. 2.1, 3.1).
 struct Macro {
   real phi;
-  real rho_a[MMAX], j_a[MMAX][3];     // eq:density1, eq:momentum1
-  real rho_f, j_f[3], u[3];           // eqn:fdensity, eqn:f1momMomentum
+  real rho_a[MMAX], j_a[MMAX][3];     // Eq. 4, Eq. 5
+  real rho_f, j_f[3], u[3];           // Eq. 37, Eq. 38
   real Pt[3][3];                      // P = sum f c c
-  real sum_g, q[3];                   // eqn:g0momTotalEnergy, q = sum g c
+  real sum_g, q[3];                   // Eq. 39, q = sum g c
   real rho_s, Y[MMAX], X[MMAX], m_mix, R, T, P;
-  real Pi[3];                         // rho u (1 - 3RT) - rho u^3/phi^2 (eqn:Pex)
+  real Pi[3];                         // rho u (1 - 3RT) - rho u^3/phi^2 (Eq. 45)
 };
 
 struct Oracle {
@@ -375,15 +375,15 @@ int node_index(const Oracle& o, int x, int y, int z) { return x + o.cfg.nx * (y 
 int wrap(int v, int n) { return ((v % n) + n) % n; }
 
 // ---------------------------------------------------------------------------
-// Thermodynamics (Sec. 2.1 nomenclature, Sec. 3.1 eq:specUa..eq:H).
+// Thermodynamics (Sec. 2.1 nomenclature, Sec. 3.1 Eq. 33..Eq. 36).
 // ---------------------------------------------------------------------------
 real R_species(const Oracle& o, int a) { return o.RU / o.m[a]; }            // R_a = R_U / m_a
-real U_species(const Oracle& o, int a, real T) {                          // eq:specUa
+real U_species(const Oracle& o, int a, real T) {                          // Eq. 33
   return o.U0[a] + o.cvf[a] * R_species(o, a) * (T - o.cfg.T_thermo);
 }
 
-// Species equilibrium (eq:27eq), quasi-equilibrium (eq:27qeq with the
-// parameterisation eq:xiPstar2) and Knudsen quasi-equilibrium (eq:fKnudsen):
+// Species equilibrium (Eq. 15), quasi-equilibrium (Eq. 16 with the
+// parameterisation Eq. 28) and Knudsen quasi-equilibrium (Eq. 18):
 // phi rho_a Prod Psi(xi, P) with the per-axis parameters given.
 void species_form(const Oracle& o, real phi, real rho_a, const real* xi, real RaT, real* out) {
   real P[3];
@@ -404,8 +404,8 @@ void compute_macro(const Oracle& o, const real* fpop /* [nl][Q] */, real phi, re
       s += f;
       for (int al = 0; al < 3; ++al) j[al] += f * L.c[i][al];
     }
-    m.rho_a[a] = s / phi;                               // eq:density1
-    for (int al = 0; al < 3; ++al) m.j_a[a][al] = j[al]; // eq:momentum1
+    m.rho_a[a] = s / phi;                               // Eq. 4
+    for (int al = 0; al < 3; ++al) m.j_a[a][al] = j[al]; // Eq. 5
   }
   {
     const real* f = fpop + o.M * o.Q;
@@ -417,7 +417,7 @@ void compute_macro(const Oracle& o, const real* fpop /* [nl][Q] */, real phi, re
         for (int be = 0; be < 3; ++be) P[al][be] += f[i] * L.c[i][al] * L.c[i][be];
       }
     }
-    m.rho_f = s / phi;                                  // eqn:fdensity
+    m.rho_f = s / phi;                                  // Eq. 37
     for (int al = 0; al < 3; ++al) { m.j_f[al] = j[al]; m.u[al] = j[al] / m.rho_f; }
     for (int al = 0; al < 3; ++al) for (int be = 0; be < 3; ++be) m.Pt[al][be] = P[al][be];
   }
@@ -438,9 +438,9 @@ void compute_macro(const Oracle& o, const real* fpop /* [nl][Q] */, real phi, re
   m.m_mix = 1.0 / inv_m;
   for (int a = 0; a < o.M; ++a) m.X[a] = m.m_mix * m.Y[a] / o.m[a];
   m.R = o.RU / m.m_mix;                                 // R = R_U / m
-  // temperature (eq:temperature with u^2/(2 phi^2), reading R5; constant C_v)
+  // temperature (Eq. 41 with u^2/(2 phi^2), reading R5; constant C_v)
   if (o.energy) {
-    real E = m.sum_g / (phi * m.rho_f);               // eq:totalE with the momentum lattice's rho (reading R7)
+    real E = m.sum_g / (phi * m.rho_f);               // Eq. 40 with the momentum lattice's rho (reading R7)
     real w2 = 0.0;
     for (int al = 0; al < o.D; ++al) w2 += (m.u[al] / phi) * (m.u[al] / phi);
     real cv = 0.0, U0m = 0.0;
@@ -453,7 +453,7 @@ void compute_macro(const Oracle& o, const real* fpop /* [nl][Q] */, real phi, re
   } else {
     m.T = Tfixed;
   }
-  m.P = m.rho_f * m.R * m.T;                            // eqn:eosIdealGas with rho of eqn:fdensity (reading R7)
+  m.P = m.rho_f * m.R * m.T;                            // Eq. 3 with rho of Eq. 37 (reading R7)
   for (int al = 0; al < 3; ++al) {
     real w = m.u[al] / phi;
     m.Pi[al] = m.rho_f * m.u[al] * (1.0 - 3.0 * m.R * m.T) - m.rho_f * m.u[al] * w * w;
@@ -464,7 +464,7 @@ void compute_macro(const Oracle& o, const real* fpop /* [nl][Q] */, real phi, re
 // Surface source (a10): mass-action kinetics, backward Euler in the reaction
 // extents over one time step by Newton iteration (readings R15, R16).
 // Returns gas mass production rates rhodot_f[a] (kg/m^3 per lattice time,
-// eq:totalFluidReactionRate / eq:molarToMassRates) and the new coverages.
+// Eq. 68 / Eq. 69) and the new coverages.
 // ---------------------------------------------------------------------------
 void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhodot_f,
                     real* Xs1, real& dU_fluid_volumetric, real& current, double dphi);
@@ -492,21 +492,21 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
     for (int b = 0; b < M; ++b) {
       if (a == b) { tau_ab[a][b] = 0.0; continue; }
       real Dab = o.Dref[a][b] * r_pow(T / o.cfg.T_ref, 1.5) * (o.Pref / P);
-      // eqn:tauab read dimensionally (reading R1): tau_ab = D_ab m_a m_b / (m R_U T)
+      // Eq. 23 read dimensionally (reading R1): tau_ab = D_ab m_a m_b / (m R_U T)
       tau_ab[a][b] = Dab * o.m[a] * o.m[b] / (m.m_mix * o.RU * T);
     }
   real inv_tau[MMAX], inv_tauk[MMAX], beta[MMAX];
   for (int a = 0; a < M; ++a) {
-    real s = 0.0;                                      // eqn:taua
+    real s = 0.0;                                      // Eq. 24
     for (int b = 0; b < M; ++b) if (b != a) s += m.Y[b] / tau_ab[a][b];
     inv_tau[a] = s;
-    // eqn:betaa: beta = dt/(2 tau + dt), written as (1/tau)/(2 + 1/tau) so that
+    // Eq. 22: beta = dt/(2 tau + dt), written as (1/tau)/(2 + 1/tau) so that
     // a species with no partner (1/tau = 0) gets beta = 0 (reading R11)
     beta[a] = inv_tau[a] / (2.0 + inv_tau[a]);
     if (o.knudsen) {
       // Knudsen diffusivity (Sec. 5.1): D^k = (phi/tortuosity)(d0/3) sqrt(8 R_U T/(pi m_a))
       real Dk = (phi / o.tort) * (o.d0 / 3.0) * r_sqrt(8.0 * o.RU * T / (PI_D * o.m[a]));
-      // eqn:tauak read dimensionally (reading R1): tau^k = D^k m_a / (R_U T)
+      // Eq. 26 read dimensionally (reading R1): tau^k = D^k m_a / (R_U T)
       real tk = Dk * o.m[a] / (o.RU * T);
       inv_tauk[a] = 1.0 / tk;
     } else {
@@ -519,15 +519,15 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   for (int a = 0; a < M; ++a)
     for (int al = 0; al < 3; ++al)
       ua[a][al] = (m.rho_a[a] < 1e-14 * m.rho_s) ? m.u[al] : m.j_a[a][al] / m.rho_a[a];   // R11
-  // eqn:transform1 with the Knudsen part taken on the component velocity
+  // Eq. 29 with the Knudsen part taken on the component velocity
   // (reading R27): the trapezoidal rule of Sec. 2.3 applied to the Knudsen
-  // relaxation (f*_a - f^k_a)/tau^k_a, whose f^k rests (eq:fKnudsen), acts on
+  // relaxation (f*_a - f^k_a)/tau^k_a, whose f^k rests (Eq. 18), acts on
   // u + V_a, not on V_a alone, which adds -(dt/2tau^k_a) u to the printed
   // right-hand side (the printed system is the u = 0 case).
   real A[MMAX * MMAX], rhs[MMAX * 3], V[MMAX * 3];
   for (int a = 0; a < M; ++a) {
     for (int b = 0; b < M; ++b) {
-      if (a == b) A[a * M + b] = 1.0 + 0.5 * inv_tau[a] + 0.5 * inv_tauk[a];   // eqn:transform1
+      if (a == b) A[a * M + b] = 1.0 + 0.5 * inv_tau[a] + 0.5 * inv_tauk[a];   // Eq. 29
       else A[a * M + b] = -0.5 * m.Y[b] / tau_ab[a][b];
     }
     for (int al = 0; al < 3; ++al)
@@ -560,19 +560,19 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   const_cast<Oracle&>(o).dg_current[n] = Iv;
   for (int a = 0; a < M; ++a) const_cast<Oracle&>(o).dg_rhodot[(size_t)a * o.N + n] = rhodot[a];
 
-  // --- species collision (a7): eqn:finalNumericalEquationsReactive ----------
+  // --- species collision (a7): Eq. 21 ----------
   real feq[MMAX][QMAX], fst[MMAX][QMAX], fk[MMAX][QMAX], fr[MMAX][QMAX];
   for (int a = 0; a < M; ++a) {
     real RaT = R_species(o, a) * T;
     real xi_eq[3], xi_st[3], xi_k[3] = {0, 0, 0};
     for (int al = 0; al < 3; ++al) {
-      xi_eq[al] = m.u[al] / phi;                         // eq:27eq
-      xi_st[al] = (m.u[al] + V[a * 3 + al]) / phi;       // eq:xiPstar2 with phi (reading R2)
+      xi_eq[al] = m.u[al] / phi;                         // Eq. 15
+      xi_st[al] = (m.u[al] + V[a * 3 + al]) / phi;       // Eq. 28 with phi (reading R2)
     }
     species_form(o, phi, m.rho_a[a], xi_eq, RaT, feq[a]);
     species_form(o, phi, m.rho_a[a], xi_st, RaT, fst[a]);
-    species_form(o, phi, m.rho_a[a], xi_k, RaT, fk[a]);  // eq:fKnudsen
-    // reaction source populations (eq:fsourceHetero): rhodot Prod Psi(u/phi, ...)
+    species_form(o, phi, m.rho_a[a], xi_k, RaT, fk[a]);  // Eq. 18
+    // reaction source populations (Eq. 89): rhodot Prod Psi(u/phi, ...)
     real pf[QMAX], Pp[3];
     for (int al = 0; al < D; ++al) Pp[al] = xi_eq[al] * xi_eq[al] + RaT;
     product_form(L, xi_eq, Pp, pf);
@@ -580,22 +580,22 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   }
   for (int a = 0; a < M; ++a) {
     for (int i = 0; i < Q; ++i) {
-      real F = 0.0;                                    // eqn:fStar
+      real F = 0.0;                                    // Eq. 25
       for (int b = 0; b < M; ++b) if (b != a) F += (1.0 / tau_ab[a][b]) * (feq[b][i] - fst[b][i]);
       F *= m.Y[a];
       F += inv_tauk[a] * (fst[a][i] - fk[a][i]);
       real f = fin[a * Q + i];
-      // R^r ~ fdot^r dt (eq:R2), dt = 1
+      // R^r ~ fdot^r dt (Eq. 32), dt = 1
       fout[a * Q + i] = f + 2.0 * beta[a] * (feq[a][i] - f) + (beta[a] - 1.0) * F + fr[a][i];
     }
   }
 
-  // --- momentum lattice (a8): eqn:f / eqn:f_source ---------------------------
-  // net Knudsen force eqn:netKnudsenForce with P X_b / D^k_b = rho_b / tau^k_b
+  // --- momentum lattice (a8): Eq. 42 / Eq. 87 ---------------------------
+  // net Knudsen force Eq. 48 with P X_b / D^k_b = rho_b / tau^k_b
   // and the component velocity u_b = u* + (V_b - Vbar) (reading R8): the
   // mixture velocity plus the diffusion velocity taken relative to the
   // species' mass average Vbar = sum_c Y_c V_c, whose mass-weighted sum
-  // vanishes as eq:totmomSpec requires.  The mixture velocity u* is the
+  // vanishes as Eq. 6 requires.  The mixture velocity u* is the
   // momentum lattice's, at the middle of the step (u* = u + dt F^k/(2 rho)):
   // the trapezoidal rule of Sec. 2.3 applied to the drag of the mixture, so
   //   F^k = -sum_b rho_b (u + V_b - Vbar)/tau^k_b / (1 + (dt/2) sum_b (rho_b/rho)/tau^k_b).
@@ -612,74 +612,74 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
   // viscosity (reading R13): mu = sum_a X_a mu_a(T), mu_a = mu_ref,a (T/Tref)^mu_exp
   real mu = 0.0;
   for (int a = 0; a < M; ++a) mu += m.X[a] * o.muref[a] * r_pow(T / o.cfg.T_ref, o.cfg.mu_exp);
-  real omega = 1.0 / (0.5 + mu / P);                   // eq:mu with dt = 1
-  real omega1 = 1.0 / (0.5 + mu / (o.cfg.Pr * P));     // eq:lambda with lambda = mu C_p / Pr
+  real omega = 1.0 / (0.5 + mu / P);                   // Eq. 65 with dt = 1
+  real omega1 = 1.0 / (0.5 + mu / (o.cfg.Pr * P));     // Eq. 67 with lambda = mu C_p / Pr
   real vs = o.cfg.bulk_ratio * mu;                      // bulk viscosity
   const_cast<Oracle&>(o).dg_omega[n] = omega;
   const_cast<Oracle&>(o).dg_omega1[n] = omega1;
   real cv_mix = 0.0;
   for (int a = 0; a < M; ++a) cv_mix += m.Y[a] * o.cvf[a] * R_species(o, a);
-  // bulk-viscosity bracket of eqn:Pex; isothermal lattices have no energy
+  // bulk-viscosity bracket of Eq. 45; isothermal lattices have no energy
   // equation, so the R/C_v part (from dT/dt) is absent there.
   real bulk = -vs + mu * (2.0 / D - (o.energy ? m.R / cv_mix : 0.0));
   real uex[3], xi_ex[3], Pex[3];
   for (int al = 0; al < 3; ++al) uex[al] = m.u[al] + Fk[al] / (omega * m.rho_f);   // reading R3
   for (int al = 0; al < D; ++al) {
-    real Peq = m.R * T + (m.u[al] / phi) * (m.u[al] / phi);                      // eqn:Peq
+    real Peq = m.R * T + (m.u[al] / phi) * (m.u[al] / phi);                      // Eq. 47
     Pex[al] = Peq + bulk * gr.divu / (phi * m.rho_f)
-              + ((2.0 - omega) / (2.0 * phi * m.rho_f * omega)) * gr.dPi[al];      // eqn:Pex
+              + ((2.0 - omega) / (2.0 * phi * m.rho_f * omega)) * gr.dPi[al];      // Eq. 45
     xi_ex[al] = uex[al] / phi;
   }
   real pfx[QMAX];
   product_form(L, xi_ex, Pex, pfx);
-  // post-collision mixture density (eq:rho_pc): phi rho_pc = phi rho + sum rhodot dt
+  // post-collision mixture density (Eq. 78): phi rho_pc = phi rho + sum rhodot dt
   real sum_rd = 0.0;
   for (int a = 0; a < M; ++a) sum_rd += rhodot[a];
   real rho_pc = m.rho_f + sum_rd / phi;
   for (int i = 0; i < Q; ++i) {
-    real fex = phi * m.rho_f * pfx[i];                                          // eq:feqmix
+    real fex = phi * m.rho_f * pfx[i];                                          // Eq. 44
     real f = fin[M * Q + i];
-    fout[M * Q + i] = f + omega * (fex - f) + (rho_pc / m.rho_f * fex - fex);     // eqn:f_source
+    fout[M * Q + i] = f + omega * (fex - f) + (rho_pc / m.rho_f * fex - fex);     // Eq. 87
   }
 
-  // --- energy lattice (a9): eqn:g / eqn:g_source -----------------------------
+  // --- energy lattice (a9): Eq. 43 / Eq. 88 -----------------------------
   if (o.energy) {
     real U = 0.0, H = 0.0, Ha[MMAX];
     for (int a = 0; a < M; ++a) {
       real Ua = U_species(o, a, T);
       Ha[a] = Ua + R_species(o, a) * T;                  // H_a = U_a + R_a T (Mayer)
-      U += m.Y[a] * Ua;                                  // eq:U
-      H += m.Y[a] * Ha[a];                               // eq:H
+      U += m.Y[a] * Ua;                                  // Eq. 35
+      H += m.Y[a] * Ha[a];                               // Eq. 36
     }
     real geq[QMAX];
     energy_equilibrium(L, phi, m.rho_f, m.u, m.R * T, U, geq);
     real w2 = 0.0;
     for (int al = 0; al < D; ++al) w2 += (m.u[al] / phi) * (m.u[al] / phi);
     real qeq[3] = {0, 0, 0};
-    for (int al = 0; al < D; ++al) qeq[al] = (H + 0.5 * w2) * m.rho_f * m.u[al];   // eqn:geq1mom
-    // equilibrium pressure tensor of the momentum lattice (eq:Peq, reading R6)
+    for (int al = 0; al < D; ++al) qeq[al] = (H + 0.5 * w2) * m.rho_f * m.u[al];   // Eq. 52
+    // equilibrium pressure tensor of the momentum lattice (Eq. 49, reading R6)
     real Peq[3][3];
     for (int al = 0; al < 3; ++al)
       for (int be = 0; be < 3; ++be)
         Peq[al][be] = phi * m.rho_f * (m.u[al] / phi) * (m.u[be] / phi) + (al == be ? phi * m.rho_f * m.R * T : 0.0);
     real qdiff[3] = {0, 0, 0}, qcorr[3] = {0, 0, 0}, qex[3] = {0, 0, 0}, qst[3] = {0, 0, 0};
     for (int al = 0; al < D; ++al) {
-      // diffusion velocities relative to the mass average: eq:totmomSpec with
+      // diffusion velocities relative to the mass average: Eq. 6 with
       // u_a = u + V_a implies sum_a rho_a V_a = 0, which the discrete system
-      // eqn:transform1 satisfies only up to the weak-coupling drift (reading R22)
+      // Eq. 29 satisfies only up to the weak-coupling drift (reading R22)
       real Vbar = 0.0;
       for (int a = 0; a < M; ++a) Vbar += m.Y[a] * V[a * 3 + al];
       real sV = 0.0, sdY = 0.0;
       for (int a = 0; a < M; ++a) { sV += Ha[a] * m.Y[a] * (V[a * 3 + al] - Vbar); sdY += Ha[a] * gr.dY[a][al]; }
-      qdiff[al] = (omega1 / (omega - omega1)) * m.rho_f * sV;                      // eq:interdiffusion
-      qcorr[al] = 0.5 * ((omega1 - 2.0) / (omega1 - omega)) * P * phi * sdY;        // eq:corrFourier
+      qdiff[al] = (omega1 / (omega - omega1)) * m.rho_f * sV;                      // Eq. 58
+      qcorr[al] = 0.5 * ((omega1 - 2.0) / (omega1 - omega)) * P * phi * sdY;        // Eq. 59
       qex[al] = m.u[al] * (omega / (omega - omega1)) * bulk * gr.divu / phi
-                - 0.5 * (m.u[al] / phi) * gr.dPi[al];                                // eqn:qex
+                - 0.5 * (m.u[al] / phi) * gr.dPi[al];                                // Eq. 60
       real uP = 0.0;
       for (int be = 0; be < D; ++be) uP += (m.u[be] / phi) * (m.Pt[al][be] - Peq[al][be]);
-      qst[al] = m.q[al] - uP + qdiff[al] + qcorr[al] + qex[al];                     // eq:gstareq1mom
+      qst[al] = m.q[al] - uP + qdiff[al] + qcorr[al] + qex[al];                     // Eq. 55
     }
-    // source distribution (eqn:g0mom_source): same equilibrium with the
+    // source distribution (Eq. 86): same equilibrium with the
     // post-reaction density and internal energy (zero change without reactions)
     real gsrc[QMAX];
     bool have_src = (o.S > 0);
@@ -691,7 +691,7 @@ void collide_node(const Oracle& o, int n, const Macro& m, const Grad& gr, const 
     for (int i = 0; i < Q; ++i) {
       int c2 = 0;
       for (int al = 0; al < D; ++al) c2 += L.c[i][al] * L.c[i][al];
-      real gst = geq[i];                                                           // eq:gstar
+      real gst = geq[i];                                                           // Eq. 54
       if (c2 == 1)
         for (int al = 0; al < D; ++al) gst += 0.5 * L.c[i][al] * (qst[al] - qeq[al]);
       real src = have_src ? (gsrc[i] - geq[i]) : 0.0;
@@ -787,7 +787,7 @@ void compute_all_macro(Oracle& o) {
   }
 }
 
-// Isotropic lattice gradient (Sec. 3.3 after eqn:qex; reading R9):
+// Isotropic lattice gradient (Sec. 3.3 after Eq. 60; reading R9):
 // d_alpha A(x) = (1/c_s^2) sum_i w_i c_i,alpha A(x + c_i), c_s^2 = 1/3.
 // Outside a non-periodic x face the neighbour value is the boundary node's
 // own value (zero-gradient ghost, reading R10).
@@ -849,12 +849,12 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
   const real dtp = o.dt;                        // physical seconds
   real cg0[MMAX], cs0[SMAX];
   for (int a = 0; a < M; ++a) cg0[a] = m.rho_a[a] / o.m[a];                 // mol/m^3 of fluid
-  for (int s = 0; s < S; ++s) cs0[s] = o.gamma * Xs0[s];                    // eq:surfaceMoleFractions
+  for (int s = 0; s < S; ++s) cs0[s] = o.gamma * Xs0[s];                    // Eq. 70
   real xi[RMAX];
   for (int k = 0; k < Rn; ++k) xi[k] = 0.0;
   real scale = o.a_s / m.phi;                   // surface area per fluid volume
   // surface concentration change per extent: 1 for a surface step, l_TPB/a^(s)
-  // for an edge step (eq:totalSurfaceReactionRate), whose extent is per TPB length
+  // for an edge step (Eq. 71), whose extent is per TPB length
   real es[RMAX];
   for (int k = 0; k < Rn; ++k) es[k] = o.edge[k] ? o.l_tpb / o.a_s : 1.0;
   for (int it = 0; it < 30; ++it) {
@@ -919,8 +919,8 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
     }
     if (alpha == 1.0 && dmax <= 1e-14 * (xmax + 1e-300)) break;
   }
-  // gas production per unit volume of porous medium over dt (eq:totalFluidReactionRate,
-  // eq:molarToMassRates), converted to kg/m^3 per lattice time step
+  // gas production per unit volume of porous medium over dt (Eq. 68,
+  // Eq. 69), converted to kg/m^3 per lattice time step
   for (int a = 0; a < M; ++a) {
     real dn = 0.0;
     for (int k = 0; k < Rn; ++k) dn += o.nu_g[k][a] * xi[k];
@@ -929,14 +929,14 @@ void surface_source(const Oracle& o, const Macro& m, const real* Xs0, real* rhod
   for (int s = 0; s < S; ++s) {
     real dn = 0.0;
     for (int k = 0; k < Rn; ++k) dn += o.nu_s[k][s] * es[k] * xi[k];
-    Xs1[s] = Xs0[s] + dn / o.gamma;               // eq:totalSurfaceReactionRate (surface and edge terms)
+    Xs1[s] = Xs0[s] + dn / o.gamma;               // Eq. 71 (surface and edge terms)
   }
-  // volumetric current (eq:volumetricCurrent): I = F l_TPB (electrons per TPB length per second)
+  // volumetric current (Eq. 74): I = F l_TPB (electrons per TPB length per second)
   real ne = 0.0;
   for (int k = 0; k < Rn; ++k)
     if (o.edge[k]) ne += o.nel[k] * xi[k];
   current = FARADAY * o.l_tpb * ne / dtp;         // A per m^3 of porous medium
-  // Unified internal energy (eq:temperatureCell, eq:InternalEnergyCell_PC): at
+  // Unified internal energy (Eq. 80, Eq. 85): at
   // fixed temperature the fluid gains what the adsorbed phase loses; molar
   // internal energies U_s(T) = U0_s + cv_s R_U (T - T_thermo).
   real dUs = 0.0;

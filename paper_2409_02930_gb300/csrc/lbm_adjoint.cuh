@@ -2,7 +2,7 @@
 // the post-collision populations after step n, they return lambda^n and
 // accumulate dJ/dphi (porosity field) and dJ/dlambda, where lambda scales
 // every Knudsen coefficient 1/tau^k_a (pore radius and tortuosity enter the
-// step only through tortuosity / pore radius, eqn:tauak with the Knudsen
+// step only through tortuosity / pore radius, Eq. 26 with the Knudsen
 // diffusivity of Sec. 5.1).
 //
 // The step f^{n+1} = C(S f^n) is differentiated in its own structure:

@@ -78,7 +78,7 @@ LBM_HD R pull_rt(const Params<R>& p, const InletTables<R>& it, const R* __restri
   const size_t N = p.N;
   if (s >= 0) return src[(size_t)(l * Q + i) * N + s];
   if (s != SRC_GHOST) return src[(size_t)(l * Q + (Q - 1 - i)) * N + (-1 - s)];
-  // reservoir equilibrium (eq:27eq / eq:feqmix / eq:geq_i at the reservoir state)
+  // reservoir equilibrium (Eq. 15 / Eq. 44 / Eq. 51 at the reservoir state)
   const int sd = gh.side;
   const R phi = gh.phi;
   const R T = it.T[sd];
@@ -212,8 +212,8 @@ LBM_HD void moments_rt(const Params<R>& p, const InletTables<R>& it, const R* __
 
 // Heterogeneous-reaction sources of one node for one step (Sec. 4.2): gas
 // mass production rhodot_a dt per unit volume of porous medium
-// (eq:totalFluidReactionRate) and the change of the fluid internal energy
-// per unit volume (eq:InternalEnergyCell_PC), in lattice energy units.
+// (Eq. 68) and the change of the fluid internal energy
+// per unit volume (Eq. 85), in lattice energy units.
 template <class R>
 struct NodeSource {
   R rhodot[MMAX];
@@ -221,8 +221,8 @@ struct NodeSource {
 };
 
 // Collision and store of one node (runtime loop form of collide_and_store).
-// With SRC the reaction sources are added: eq:fsourceHetero to the species,
-// eqn:f_source to the momentum lattice and eqn:g_source to the energy lattice.
+// With SRC the reaction sources are added: Eq. 89 to the species,
+// Eq. 87 to the momentum lattice and Eq. 88 to the energy lattice.
 // With COEF, coef[l] receives the derivative of every non-rest post-collision
 // population of lattice l with respect to its own streamed population at
 // fixed moments (1 - 2 beta_a for the species, 1 - omega for the momentum and
@@ -246,7 +246,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
 #pragma unroll
   for (int b = 0; b < D; ++b) w[b] = s.u[b] * inv_phi;
 
-  // mixture transport (eq:mu, eq:lambda)
+  // mixture transport (Eq. 65, Eq. 67)
   R mu = R(0);
   {
     R pw = pow_<R>(s.T * p.inv_T_ref, p.mu_exp);
@@ -265,7 +265,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
   const R bulk = -p.bulk_ratio * mu + mu * (R(2) / R(D) - (EN ? s.Rg / s.cv : R(0)));
 
   // per-axis factors of the species equilibria, quasi-equilibria and
-  // Knudsen states (eq:27eq, eq:27qeq with eq:xiPstar2, eq:fKnudsen)
+  // Knudsen states (Eq. 15, Eq. 16 with Eq. 28, Eq. 18)
   R E[M][D][3], S[M][D][3], K[M][3], pr[M];
 #pragma unroll
   for (int a = 0; a < M; ++a) {
@@ -279,7 +279,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
     psi3<R>(R(0), RaT, K[a]);
     pr[a] = phi * s.rho_a[a];
   }
-  // momentum lattice factors (eq:feqmix, eqn:Pex, reading of u^ex)
+  // momentum lattice factors (Eq. 44, Eq. 45, reading of u^ex)
   R FX[D][3];
   {
     const R irf = R(1) / (phi * s.rho_f);
@@ -305,7 +305,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
     }
   }
   const R pref_f = phi * s.rho_f;
-  // post-collision density (eq:rho_pc) and the eqn:f_source factor
+  // post-collision density (Eq. 78) and the Eq. 87 factor
   R rho_pc = s.rho_f, kpc = R(0);
   if (SRC) {
     R sum_rd = R(0);
@@ -314,7 +314,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
     rho_pc = s.rho_f + sum_rd * inv_phi;
     kpc = rho_pc / s.rho_f - R(1);
   }
-  // energy lattice (eqn:g with eq:gstar, multiplied through by omega - omega1)
+  // energy lattice (Eq. 43 with Eq. 54, multiplied through by omega - omega1)
   GeqFactors<R, D> G, G2;
   R Dq[D];
   R g_src_total = R(0);
@@ -333,7 +333,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
     for (int b = 0; b < D; ++b) w2 += w[b] * w[b];
     G.init(phi, s.rho_f, s.u, RT, U);
     if (SRC) {
-      // source distribution with the post-reaction density and internal energy (eqn:g0mom_source)
+      // source distribution with the post-reaction density and internal energy (Eq. 86)
       const R U_pc = (phi * s.rho_f * U + srcv->dU) / (phi * rho_pc);
       G2.init(phi, rho_pc, s.u, RT, U_pc);
       g_src_total = phi * rho_pc * (U_pc + R(0.5) * w2) - phi * s.rho_f * (U + R(0.5) * w2);
@@ -368,7 +368,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
   for_each_dir<D, PullF::kUnroll>([&](int i, int cx, int cy, int cz) {
     if (i == REST) return;
     const int h = pf.prep(cx, cy, cz);
-    // species (eqn:finalNumericalEquationsReactive, eqn:fStar)
+    // species (Eq. 21, Eq. 25)
     R feq[M], fst[M], fk[M];
 #pragma unroll
     for (int a = 0; a < M; ++a) {
@@ -400,23 +400,23 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
         R shape = E[a][0][cx + 1];
         if (D >= 2) shape *= sel3(E[a][1], cy);
         if (D == 3) shape *= sel3(E[a][D - 1], cz);
-        out += srcv->rhodot[a] * shape;                  // eq:fsourceHetero, R^r = fdot^r dt
+        out += srcv->rhodot[a] * shape;                  // Eq. 89, R^r = fdot^r dt
       }
       acc[a] += out;
       dst[(size_t)(a * Q + i) * N + n] = out;
     }
-    // momentum (eqn:f)
+    // momentum (Eq. 42)
     {
       R fex = pref_f * FX[0][cx + 1];
       if (D >= 2) fex *= sel3(FX[1], cy);
       if (D == 3) fex *= sel3(FX[D - 1], cz);
       R f = pf.get(h, M, i, cx, cy, cz);
       R out = f + omega * (fex - f);
-      if (SRC) out += kpc * fex;                          // eqn:f_source
+      if (SRC) out += kpc * fex;                          // Eq. 87
       acc[M] += out;
       dst[(size_t)(M * Q + i) * N + n] = out;
     }
-    // energy (eqn:g, eq:geq_i, eq:gstar)
+    // energy (Eq. 43, Eq. 51, Eq. 54)
     if (EN) {
       const int cc[3] = {cx, cy, cz};
       R prod = R(1), s2 = R(0);
@@ -433,7 +433,7 @@ LBM_HD void collide_gen(const Params<R>& p, const PullF& pf, int n, const Moment
       R geq = G.pref_U * prod + G.pref * s2;
       R g = pf.get(h, M + 1, i, cx, cy, cz);
       R out = g + omega * (geq - g);
-      if (SRC) {                                          // eqn:g_source
+      if (SRC) {                                          // Eq. 88
         R prod2 = R(1), s22 = R(0);
 #pragma unroll
         for (int b = 0; b < D; ++b) prod2 *= sel3(G2.P1[b], cc[b]);

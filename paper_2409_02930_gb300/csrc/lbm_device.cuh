@@ -1,16 +1,16 @@
 // Device-side physics of the mean-field porous-media LBM step (sm_103a).
 //
 // Every per-node quantity follows Sawant & Karlin, arXiv 2409.02930:
-//   species lattices      Sec. 2.2-2.3 (eq:27eq, eq:27qeq, eq:fKnudsen,
-//                         eqn:finalNumericalEquationsReactive, eqn:betaa,
-//                         eqn:tauab, eqn:taua, eqn:fStar, eqn:tauak,
-//                         eq:xiPstar2, eqn:transform1)
-//   momentum lattice      Sec. 3.2 (eqn:f, eq:feqmix, eqn:Pex, eqn:Peq,
-//                         eqn:netKnudsenForce)
-//   energy lattice        Sec. 3.3 (eqn:g, eq:geq_i, eq:gstar,
-//                         eq:gstareq1mom, eq:interdiffusion, eq:corrFourier,
-//                         eqn:qex)
-//   transport             eq:mu, eq:lambda; Knudsen diffusivity of Sec. 5.1
+//   species lattices      Sec. 2.2-2.3 (Eq. 15, Eq. 16, Eq. 18,
+//                         Eq. 21, Eq. 22,
+//                         Eq. 23, Eq. 24, Eq. 25, Eq. 26,
+//                         Eq. 28, Eq. 29)
+//   momentum lattice      Sec. 3.2 (Eq. 42, Eq. 44, Eq. 45, Eq. 47,
+//                         Eq. 48)
+//   energy lattice        Sec. 3.3 (Eq. 43, Eq. 51, Eq. 54,
+//                         Eq. 55, Eq. 58, Eq. 59,
+//                         Eq. 60)
+//   transport             Eq. 65, Eq. 67; Knudsen diffusivity of Sec. 5.1
 // The readings taken where the paper is ambiguous are the library's
 // documented ones (dimensional tau_ab and tau^k; porosity-weighted
 // quasi-equilibrium and energy operator; u^ex = u + dt F^k/(omega rho);
@@ -55,7 +55,7 @@ struct Params {
 };
 
 // ---------------------------------------------------------------------------
-// velocity set helpers (c_i of eq:d3q27vel; i = (cx+1) + 3(cy+1) + 9(cz+1))
+// velocity set helpers (c_i of Eq. 10; i = (cx+1) + 3(cy+1) + 9(cz+1))
 // ---------------------------------------------------------------------------
 template <int D> struct Lat { static constexpr int Q = (D == 3) ? 27 : 9; };
 
@@ -72,7 +72,7 @@ template <int D> __host__ __device__ constexpr int csq_of(int i) {
   return c_of<D>(i, 0) * c_of<D>(i, 0) + c_of<D>(i, 1) * c_of<D>(i, 1) + c_of<D>(i, 2) * c_of<D>(i, 2);
 }
 
-// Product-form factor Psi_c(xi, P) (eqn:phi0, eqn:phiPlus, eqn:phis).
+// Product-form factor Psi_c(xi, P) (Eq. 11, Eq. 12, Eq. 13).
 template <class R>
 LBM_HD R psi(int c, R xi, R P) {
   return c == 0 ? (R(1) - P) : R(0.5) * (R(c) * xi + P);
@@ -106,8 +106,8 @@ template <class R> LBM_HD bool finite_(R v) { return v == v && v - v == v - v; }
 LBM_HD int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
 // ---------------------------------------------------------------------------
-// Energy equilibrium (eq:geq_i) in closed form.  The operator O_alpha of
-// eqn:oalpha acts in w = u/phi; on the generating function
+// Energy equilibrium (Eq. 51) in closed form.  The operator O_alpha of
+// Eq. 50 acts in w = u/phi; on the generating function
 // E = U + sum_beta w_beta^2/2 it gives, per axis,
 //   O 1 = w, O^2 1 = RT + w^2                         (the factors P1)
 //   O (w^2/2) = RT w + w^3/2, O^2 (w^2/2) = RT^2 + 5/2 RT w^2 + w^4/2

@@ -3,7 +3,7 @@
 // A block owns a tile of TX (x) by TY (y, 3-D only) nodes and marches along
 // the slowest axis (y in 2-D, z in 3-D) over SEG planes.  For every plane it
 // first recomputes, from the streamed populations, the macroscopic fields
-// that the isotropic gradients need (u, Pi_alpha of eqn:Pex, Y_a) on the tile
+// that the isotropic gradients need (u, Pi_alpha of Eq. 45, Y_a) on the tile
 // plus a one-node halo, into a rolling shared-memory ring of three planes;
 // then it collides the interior nodes of the previous plane, whose stencil
 // now lies entirely in the ring.  No macro field goes through global memory,

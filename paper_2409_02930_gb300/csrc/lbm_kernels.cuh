@@ -38,7 +38,7 @@ LBM_HD void node_xyz(const Params<R>& p, int n, int& x, int& y, int& z) {
 
 // ---------------------------------------------------------------------------
 // Pass 1 (two-pass form): macroscopic fields needed by the neighbours'
-// gradients -- u, Pi_alpha of eqn:Pex and Y_a (eq:corrFourier).
+// gradients -- u, Pi_alpha of Eq. 45 and Y_a (Eq. 59).
 // ---------------------------------------------------------------------------
 template <class R, int D, int M, bool EN>
 LBM_HD void macro_node(const Params<R>& p, const InletTables<R>& it, const StepArgs<R>& a, int n) {
@@ -130,7 +130,7 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
 #pragma unroll
   for (int b = 0; b < D; ++b) w[b] = s.u[b] * inv_phi;
 
-  // ---- species (eqn:finalNumericalEquationsReactive with eqn:fStar) -------
+  // ---- species (Eq. 21 with Eq. 25) -------
   {
     R E[M][D][3], S[M][D][3], K[M][3], pr[M];
 #pragma unroll
@@ -138,11 +138,11 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
       R RaT = p.Ra[a] * s.T;
 #pragma unroll
       for (int b = 0; b < D; ++b) {
-        psi3<R>(w[b], w[b] * w[b] + RaT, E[a][b]);                  // eq:27eq
-        R xs = (s.u[b] + tr.V[a][b]) * inv_phi;                      // eq:xiPstar2 over phi
-        psi3<R>(xs, xs * xs + RaT, S[a][b]);                         // eq:27qeq
+        psi3<R>(w[b], w[b] * w[b] + RaT, E[a][b]);                  // Eq. 15
+        R xs = (s.u[b] + tr.V[a][b]) * inv_phi;                      // Eq. 28 over phi
+        psi3<R>(xs, xs * xs + RaT, S[a][b]);                         // Eq. 16
       }
-      psi3<R>(R(0), RaT, K[a]);                                      // eq:fKnudsen
+      psi3<R>(R(0), RaT, K[a]);                                      // Eq. 18
       pr[a] = phi * s.rho_a[a];
     }
     // The rest population is written last as the remainder of the streamed
@@ -185,7 +185,7 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
     for (int a = 0; a < M; ++a) dst[(size_t)(a * Q + REST) * N + n] = mo.sa[a] - acc[a];
   }
 
-  // ---- transport of the mixture (eq:mu, eq:lambda) --------------------------
+  // ---- transport of the mixture (Eq. 65, Eq. 67) --------------------------
   R mu = R(0);
   {
     R pw = pow_<R>(s.T * p.inv_T_ref, p.mu_exp);
@@ -197,7 +197,7 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
   const R omega1 = R(1) / (R(0.5) + mu * p.inv_Pr / s.P);
   const R bulk = -p.bulk_ratio * mu + mu * (R(2) / R(D) - (EN ? s.Rg / s.cv : R(0)));
 
-  // ---- momentum lattice (eqn:f, eq:feqmix, eqn:Pex, eqn:netKnudsenForce) ----
+  // ---- momentum lattice (Eq. 42, Eq. 44, Eq. 45, Eq. 48) ----
   {
     R FX[D][3];
     const R irf = R(1) / (phi * s.rho_f);
@@ -238,7 +238,7 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
     dst[(size_t)(M * Q + REST) * N + n] = mo.sf - acc;
   }
 
-  // ---- energy lattice (eqn:g with eq:gstar, multiplied through by omega - omega1)
+  // ---- energy lattice (Eq. 43 with Eq. 54, multiplied through by omega - omega1)
   if (EN) {
     R U = R(0), Ha[M];
 #pragma unroll
@@ -257,11 +257,11 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
     R Dq[D];
 #pragma unroll
     for (int b = 0; b < D; ++b) {
-      R qeq = (H + R(0.5) * w2) * s.rho_f * s.u[b];                    // eqn:geq1mom
+      R qeq = (H + R(0.5) * w2) * s.rho_f * s.u[b];                    // Eq. 52
       R uP = R(0);
 #pragma unroll
       for (int c = 0; c < D; ++c) {
-        R Peq = s.rho_f * s.u[b] * w[c] + (b == c ? phi * s.rho_f * RT : R(0));   // eq:Peq
+        R Peq = s.rho_f * s.u[b] * w[c] + (b == c ? phi * s.rho_f * RT : R(0));   // Eq. 49
         uP += w[c] * (mo.Pt[b][c] - Peq);
       }
       R Vbar = R(0);
@@ -273,7 +273,7 @@ LBM_HD void collide_and_store(const Params<R>& p, const Puller<R, D, M, EN>& pl,
         sV += Ha[a] * s.Y[a] * (tr.V[a][b] - Vbar);
         sdY += Ha[a] * gr.dY[a][b];
       }
-      // (omega - omega1) (q* - q^eq) with q^diff, q^corr, q^ex of eq:gstareq1mom
+      // (omega - omega1) (q* - q^eq) with q^diff, q^corr, q^ex of Eq. 55
       Dq[b] = (omega - omega1) * (mo.q[b] - uP - qeq) + omega1 * s.rho_f * sV +
               R(0.5) * (R(2) - omega1) * s.P * phi * sdY + s.u[b] * omega * bulk * gr.divu * inv_phi -
               R(0.5) * (omega - omega1) * w[b] * gr.dPi[b];
@@ -325,11 +325,11 @@ __global__ void __launch_bounds__(256) k_collide(Params<R> p, InletTables<R> it,
 }
 
 // ---------------------------------------------------------------------------
-// Initial populations: equilibria of the initial fields (eq:27eq, eq:feqmix
-// without extension, eq:geq_i).
+// Initial populations: equilibria of the initial fields (Eq. 15, Eq. 44
+// without extension, Eq. 51).
 // ---------------------------------------------------------------------------
-// Initial populations of node n: equilibria of the initial fields (eq:27eq,
-// eq:feqmix without extension, eq:geq_i).  R is the computing type, PR the
+// Initial populations of node n: equilibria of the initial fields (Eq. 15,
+// Eq. 44 without extension, Eq. 51).  R is the computing type, PR the
 // parameter type; store(l, i, value).
 template <class R, int D, int M, bool EN, class PR, class Store>
 LBM_HD void init_node(const PR& p, const double* __restrict__ X, const double* __restrict__ T0,

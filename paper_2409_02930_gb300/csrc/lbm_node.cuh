@@ -141,8 +141,8 @@ struct Puller {
   }
 };
 
-// Moments of the streamed populations (eq:density1, eq:momentum1,
-// eqn:fdensity, eqn:f1momMomentum, eqn:g0momTotalEnergy, q, P).
+// Moments of the streamed populations (Eq. 4, Eq. 5,
+// Eq. 37, Eq. 38, Eq. 39, q, P).
 template <class R, int D, int M, bool EN, bool FULL>
 struct Moments {
   R sa[M], ja[M][D];
@@ -220,8 +220,8 @@ struct State {
     rho_s = R(0);
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-      rho_a[a] = mo.sa[a] * inv_phi;          // eq:density1
-      rho_s += rho_a[a];                      // eq:rhoSpec
+      rho_a[a] = mo.sa[a] * inv_phi;          // Eq. 4
+      rho_s += rho_a[a];                      // Eq. 1
     }
     R inv_rs = R(1) / rho_s;
     R inv_m = R(0);
@@ -234,14 +234,14 @@ struct State {
 #pragma unroll
     for (int a = 0; a < M; ++a) X[a] = m_mix * Y[a] / p.m[a];
     Rg = p.RU * inv_m;                        // R = R_U / m
-    rho_f = mo.sf * inv_phi;                  // eqn:fdensity
+    rho_f = mo.sf * inv_phi;                  // Eq. 37
 #pragma unroll
     for (int b = 0; b < D; ++b) u[b] = mo.jf[b] / rho_f;
     cv = R(0);
 #pragma unroll
     for (int a = 0; a < M; ++a) cv += Y[a] * p.cvR[a];
     if (EN) {
-      // eq:temperature with constant C_v and u^2/(2 phi^2)
+      // Eq. 41 with constant C_v and u^2/(2 phi^2)
       R E = mo.sg / (phi * rho_f);
       R w2 = R(0), U0m = R(0);
 #pragma unroll
@@ -253,18 +253,18 @@ struct State {
     } else {
       T = Tfixed;
     }
-    P = rho_f * Rg * T;                       // eqn:eosIdealGas
+    P = rho_f * Rg * T;                       // Eq. 3
   }
 
-  // Pi_alpha = rho u_alpha (1 - 3RT) - rho u_alpha^3 / phi^2 (eqn:Pex)
+  // Pi_alpha = rho u_alpha (1 - 3RT) - rho u_alpha^3 / phi^2 (Eq. 45)
   LBM_HD R Pi(int b) const {
     R w = u[b] / phi;
     return rho_f * u[b] * (R(1) - R(3) * Rg * T) - rho_f * u[b] * w * w;
   }
 };
 
-// Transport coefficients (eqn:tauab, eqn:taua, eqn:betaa, eqn:tauak) and the
-// diffusion-velocity solve (eqn:transform1).
+// Transport coefficients (Eq. 23, Eq. 24, Eq. 22, Eq. 26) and the
+// diffusion-velocity solve (Eq. 29).
 template <class R, int D, int M>
 struct Transport {
   R inv_tau_ab[M][M];

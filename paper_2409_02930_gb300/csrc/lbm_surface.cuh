@@ -8,11 +8,11 @@
 // Rates, residual and extents are FP64 whatever the population precision;
 // the Jacobian is FP64 on the FP64 path and FP32 on the FP32 path, and is
 // reused across iterations (iterative refinement to the same FP64 root).  Then the gas mass production
-// (eq:totalFluidReactionRate, eq:molarToMassRates), the new coverages
-// (eq:surfaceMoleFractions, eq:totalSurfaceReactionRate with the TPB edge
-// steps), the volumetric current (eq:volumetricCurrent) and the change of the
+// (Eq. 68, Eq. 69), the new coverages
+// (Eq. 70, Eq. 71 with the TPB edge
+// steps), the volumetric current (Eq. 74) and the change of the
 // fluid internal energy: the unified internal energy of fluid and adsorbed
-// phases (eq:temperatureCell, eq:InternalEnergyCell_PC) gains the ohmic heat
+// phases (Eq. 80, Eq. 85) gains the ohmic heat
 // and loses the electric power of the current (Sec. 4.2).
 #pragma once
 

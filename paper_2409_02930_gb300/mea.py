@@ -2,10 +2,10 @@
 step (Sec. 4.1): the serial outer loops of the membrane-electrode assembly.
 
 Along the cell direction x the electrode phase has one potential
-(eq:electrodePotential), the volumetric current of the triple-phase
+(Eq. 75), the volumetric current of the triple-phase
 boundary I_v(x) integrates to the current density I_a(x)
-(eq:areaCurrentDensity), and Ohm's law in the electrolyte phase integrates
-I_a Omega to the electrolyte potential (eq:electrolytePotential), zero at
+(Eq. 76), and Ohm's law in the electrolyte phase integrates
+I_a Omega to the electrolyte potential (Eq. 77), zero at
 the start of the active section (x = 0 here, the gas side).  The TPB steps
 see Phi_electrode - Phi_electrolyte(x).  The integrals are taken over the
 lattice's cells (reading R30): I_a on the face after column i is the sum of
@@ -32,13 +32,13 @@ import numpy as np
 
 
 def current_density(Iv_x: np.ndarray, dx: float) -> np.ndarray:
-    """I_a on the face after each column [A/m^2] (eq:areaCurrentDensity)."""
+    """I_a on the face after each column [A/m^2] (Eq. 76)."""
     return np.cumsum(np.asarray(Iv_x, float)) * dx
 
 
 def electrolyte_potential(Ia_faces: np.ndarray, omega_x, dx: float) -> np.ndarray:
     """Electrolyte potential of each column [V], zero at column 0
-    (eq:electrolytePotential): the ohmic drops I_a Omega dx over the faces
+    (Eq. 77): the ohmic drops I_a Omega dx over the faces
     before it."""
     Ia = np.asarray(Ia_faces, float)
     om = np.broadcast_to(np.asarray(omega_x, float), Ia.shape)

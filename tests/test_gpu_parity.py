@@ -160,7 +160,7 @@ def test_fp32_matches_oracle(L, case):
 
 
 def test_fp32_with_the_fp64_diffusion_solve(L):
-    """The FP32 path switches the diffusion-velocity system (eqn:transform1)
+    """The FP32 path switches the diffusion-velocity system (Eq. 29)
     to double precision, assembled in double from the FP32 moments, where
     its condition bound exceeds kappa_threshold.  A tiny threshold sends
     every node there: the run differs from the plain FP32 run (the branch is

@@ -14,8 +14,8 @@ F_C = 96485.33212
 
 def test_uniform_current_gives_linear_current_density_and_quadratic_potential():
     """I_v uniform: I_a after column i is (i+1) I_v dx, and the electrolyte
-    potential of column i is I_v Omega dx^2 i (i+1)/2 (eq:areaCurrentDensity,
-    eq:electrolytePotential summed over the cells, reading R30)."""
+    potential of column i is I_v Omega dx^2 i (i+1)/2 (Eq. 76,
+    Eq. 77 summed over the cells, reading R30)."""
     n, dx, Iv, om = 7, 2.5e-6, 3.0e9, 0.3
     Ia = mea.current_density(np.full(n, Iv), dx)
     np.testing.assert_allclose(Ia, (np.arange(n) + 1) * Iv * dx, rtol=1e-14)

@@ -28,7 +28,7 @@ def _lattice(D):
 @pytest.mark.parametrize("D", [2, 3])
 def test_product_form_moments(D):
     """Sum_i Psi_i = 1, Sum Psi c = xi, Sum Psi c_a^2 = P_aa,
-    Sum Psi c_a c_b = xi_a xi_b (a != b) follow from eqn:phi0..eq:prod."""
+    Sum Psi c_a c_b = xi_a xi_b (a != b) follow from Eq. 11..Eq. 14."""
     rng = np.random.default_rng(0)
     c, _ = _lattice(D)
     for _ in range(20):
@@ -72,10 +72,10 @@ def test_standard_weights(D):
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("D", [2, 3])
 def test_energy_equilibrium_printed_moments(D):
-    """g^eq of eq:geq_i reproduces eq:totalE (zeroth moment), eqn:geq1mom
-    q^eq = (H + u^2/2phi^2) rho u and eqn:geq2mom
+    """g^eq of Eq. 51 reproduces Eq. 40 (zeroth moment), Eq. 52
+    q^eq = (H + u^2/2phi^2) rho u and Eq. 53
     R^eq = (H + u^2/2phi^2) P^eq + (P/phi) u u, with H = U + RT, P = rho R T and
-    P^eq = rho u u / phi + phi P I (eq:Peq)."""
+    P^eq = rho u u / phi + phi P I (Eq. 49)."""
     rng = np.random.default_rng(1)
     c, _ = _lattice(D)
     for _ in range(20):
@@ -129,8 +129,8 @@ def test_householder_qr_solve_matches_lapack():
 # ---------------------------------------------------------------------------
 @pytest.mark.parametrize("case", ["slab", "capillary"])
 def test_collision_invariants(case):
-    """Per node, without reactions: each species mass (eqn:finalNumerical...
-    with Sum F = 0), mixture mass (eqn:f), energy (eqn:g) are conserved exactly
+    """Per node, without reactions: each species mass (Eq. 21
+    with Sum F = 0), mixture mass (Eq. 42), energy (Eq. 43) are conserved exactly
     and the momentum lattice gains exactly dt F^k (reading R3)."""
     if case == "slab":
         wl = W.slab(nx=24, ny=20)
@@ -185,7 +185,7 @@ def _periodic_line(nx, X, T=300.0, P=W.ATM, energy=False, knudsen=False, U=None,
 
 
 def test_shear_wave_viscosity():
-    """u_y = U sin(kx) decays at nu k^2 with nu = mu/rho: eq:mu's omega gives
+    """u_y = U sin(kx) decays at nu k^2 with nu = mu/rho: Eq. 65's omega gives
     back the input viscosity of pure species A (He-like, 300 K, 1 atm)."""
     nx = 64
     x = np.arange(nx)
@@ -210,8 +210,8 @@ def test_shear_wave_viscosity():
 def test_sound_wave_bulk_viscosity_and_galilean_correction():
     """Isothermal standing sound wave of pure species B (Ar-like, R T = 1/30 in
     lattice units, far from the lattice's native 1/3): acoustic energy decays at
-    (mu (2 - 2/D) + varsigma) k^2 / rho (eq:NSmix).  The bulk-viscosity bracket
-    and the d_alpha(rho u (1 - 3RT)) extension of eqn:Pex are both needed to
+    (mu (2 - 2/D) + varsigma) k^2 / rho (Eq. 64).  The bulk-viscosity bracket
+    and the d_alpha(rho u (1 - 3RT)) extension of Eq. 45 are both needed to
     get this rate with varsigma = 3 mu."""
     nx = 64
     x = np.arange(nx)
@@ -240,7 +240,7 @@ def test_sound_wave_bulk_viscosity_and_galilean_correction():
 def test_thermal_diffusivity():
     """Entropy mode T = T0 + dT sin(kx) at uniform pressure in an equimolar
     binary mixture decays at alpha k^2, alpha = lambda/(rho C_p) with lambda
-    from eq:lambda (lambda = mu C_p / Pr for the synthetic transport model);
+    from Eq. 67 (lambda = mu C_p / Pr for the synthetic transport model);
     the mixture molar mass of an equimolar mixture is (m_A + m_B)/2."""
     nx = 64
     x = np.arange(nx)
@@ -287,7 +287,7 @@ def _binary_diffusion_error(nx):
 def test_binary_diffusion_coefficient():
     """Mole-fraction wave X_A = 1/2 + eps sin(kx) (Knudsen off) decays at
     D_AB k^2 with the input D_AB, with second-order convergence in k: pins the
-    dimensional reading R1 of eqn:tauab (the printed, inverted form is off by
+    dimensional reading R1 of Eq. 23 (the printed, inverted form is off by
     orders of magnitude)."""
     e64 = _binary_diffusion_error(64)
     e128 = _binary_diffusion_error(128)
@@ -299,8 +299,8 @@ def test_interdiffusion_stays_isothermal():
     """Ideal-gas interdiffusion at uniform temperature and pressure has no
     heat of mixing, so T must stay uniform up to the small acoustic transient
     of the start (about 1-2 K here, shrinking under refinement).  This needs
-    both the interdiffusion flux (eq:interdiffusion) and the Fourier correction
-    (eq:corrFourier) in q* (eq:gstareq1mom): dropping either, or flipping the
+    both the interdiffusion flux (Eq. 58) and the Fourier correction
+    (Eq. 59) in q* (Eq. 55): dropping either, or flipping the
     sign of the correction, drifts the temperature by 10-60 K in this run."""
     nx = 64
     x = np.arange(nx)
@@ -346,7 +346,7 @@ def _capillary_steady(phi, tort, rp, nx=64, P=W.ATM, dx=1.0e-6):
 
 
 def _closed_form_errors(wl, N, X, P=W.ATM, T=300.0):
-    """Relative errors of N_A against the integrated isobaric eq:constit2
+    """Relative errors of N_A against the integrated isobaric Eq. 20
     between the quarter points, and of Graham's ratio -N_B/N_A against
     sqrt(m_A/m_B)."""
     nx = wl.nx
@@ -367,7 +367,7 @@ def _closed_form_errors(wl, N, X, P=W.ATM, T=300.0):
 def test_capillary_dusty_gas_closed_form():
     """Steady binary counter-diffusion between pure-A and pure-B reservoirs
     (Sec. 5.1 set-up, reservoir reading R10) against the integrated
-    eq:constit2 for an isobaric tube: Graham's law N_B/N_A = -sqrt(m_A/m_B)
+    Eq. 20 for an isobaric tube: Graham's law N_B/N_A = -sqrt(m_A/m_B)
     and N_A = c phi D_AB/(alpha L) ln[(1 - alpha X_A(x2) + r)/(1 - alpha X_A(x1) + r)],
     alpha = 1 - sqrt(m_A/m_B), r = D_AB/D^k_A, between two interior nodes.
 
@@ -419,7 +419,7 @@ def test_capillary_knudsen_regime_converges_to_closed_form():
 # ---------------------------------------------------------------------------
 def test_d3q27_reduces_to_d2q9_for_divergence_free_flow():
     """D3Q27 with fields uniform in z equals D2Q9 (Sum_c Psi_c = 1 per axis)
-    whenever div u = 0: only the bulk bracket of eqn:Pex carries the
+    whenever div u = 0: only the bulk bracket of Eq. 45 carries the
     dimension D.  Shear wave in a binary mixture with porosity 0.5, Knudsen
     and the energy lattice on."""
     nx = 16

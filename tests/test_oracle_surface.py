@@ -1,7 +1,7 @@
-"""Pins of the oracle's heterogeneous surface source (Sec. 4, eq:totalFluidReactionRate,
-eq:surfaceMoleFractions, eq:totalSurfaceReactionRate, eq:rho_pc,
-eq:temperatureCell / eq:InternalEnergyCell_PC, eqn:f_source, eqn:g_source,
-eq:fsourceHetero) against conservation laws the mechanism fixes."""
+"""Pins of the oracle's heterogeneous surface source (Sec. 4, Eq. 68,
+Eq. 70, Eq. 71, Eq. 78,
+Eq. 80 / Eq. 85, Eq. 87, Eq. 88,
+Eq. 89) against conservation laws the mechanism fixes."""
 import numpy as np
 import pytest
 
@@ -52,9 +52,9 @@ def test_surface_source_conserves_elements_and_sites():
 
 
 def test_surface_source_species_mass_enters_species_lattices():
-    """Per node, the species lattice gains exactly rhodot (eq:fsourceHetero,
+    """Per node, the species lattice gains exactly rhodot (Eq. 89,
     Sum_i fdot^r_ai = rhodot_a) and the momentum lattice the same total mass
-    (eqn:f_source with eq:rho_pc)."""
+    (Eq. 87 with Eq. 78)."""
     wl = _periodic_reactive()
     o = oracle.Oracle(wl)
     o.step(3)
@@ -70,7 +70,7 @@ def test_surface_source_species_mass_enters_species_lattices():
 
 def test_unified_internal_energy_is_conserved():
     """Without electrochemistry the unified internal energy of fluid and
-    adsorbed phases (eq:temperatureCell) changes only by the kinetic energy
+    adsorbed phases (Eq. 80) changes only by the kinetic energy
     of the exchanged mass, O(u^2) of the exchange."""
     wl = _periodic_reactive()
     mech = wl.mechanism
@@ -99,7 +99,7 @@ def test_unified_internal_energy_is_conserved():
 # closed forms of the backward-Euler extents (reading R16) for mechanisms
 # small enough to solve by hand: these fix the reactant orders, the
 # Arrhenius constant k = A exp(-Ea/(R_U T)) with Ea in J/mol, the gas-side
-# scale a^(s)/phi of eq:totalFluidReactionRate and backward (not forward)
+# scale a^(s)/phi of Eq. 68 and backward (not forward)
 # Euler
 # ---------------------------------------------------------------------------
 T_RX, PHI_RX, A_S, GAMMA = 1000.0, 0.5, 1.0e7, 2.6e-5
@@ -145,7 +145,7 @@ def test_adsorption_extent_is_the_backward_euler_root():
     xi = dt k (c0 - alpha xi)(theta0 - xi), alpha = a^(s)/phi: the smaller
     root of dt k alpha xi^2 - (1 + dt k (c0 + alpha theta0)) xi + dt k c0 theta0 = 0.
     The coverage of A(s) grows by xi/Gamma and the gas density of A falls by
-    a^(s) m_A xi / phi (eq:totalFluidReactionRate, eq:molarToMassRates)."""
+    a^(s) m_A xi / phi (Eq. 68, Eq. 69)."""
     probe = oracle.Oracle(_uniform_reactive([[-1, 0]], [[-1, 1]], [1.0], [0.0], [0.9, 0.1]))
     dt = probe.dt
     c0 = 0.5 * W.ATM / (R_U * T_RX)
@@ -229,10 +229,10 @@ def test_tpb_step_extent_current_and_potential(dphi):
     """H(s) + O(s) -> OH(s) + s + e on the TPB edge (rate per unit TPB
     length r = k theta_H theta_O, k = A exp(-Ea/RT) exp(beta n F dphi/RT),
     reading R29).  Its extent xi [mol/m] changes the surface concentrations
-    by lambda xi, lambda = l_TPB/a^(s) (eq:totalSurfaceReactionRate), so one
+    by lambda xi, lambda = l_TPB/a^(s) (Eq. 71), so one
     backward-Euler step solves xi = dt k (thH - lambda xi)(thO - lambda xi);
     the coverage of OH(s) grows by lambda xi/Gamma and the volumetric current
-    is I = F l_TPB xi/dt (eq:volumetricCurrent)."""
+    is I = F l_TPB xi/dt (Eq. 74)."""
     nu_s = [[1, -1, -1, 1]]                  # s, H(s), O(s), OH(s): H + O -> OH + s
     X0 = [0.7, 0.1, 0.15, 0.05]
     probe = oracle.Oracle(_uniform_reactive([[0, 0]], nu_s, [1.0], [0.0], X0,

@@ -1,5 +1,5 @@
 """Pins of the oracle's steady dusty-gas boundary-value solver (Sec. 5.1,
-eq:constit2), the reference for the ternary capillary sweep: it must reduce
+Eq. 20), the reference for the ternary capillary sweep: it must reduce
 to the integrated binary closed form when a species is absent, to pure
 Knudsen diffusion when the binary diffusivities are large, obey Graham's
 law between equal pressures, and carry the profile exactly from one end to

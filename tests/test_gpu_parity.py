@@ -38,6 +38,33 @@ def bounceback_slab(nx=40, ny=24, steps=150):
     return wl
 
 
+def species_absent(nx=32, ny=16, steps=100):
+    """Three species of which the third is absent everywhere (density exactly
+    zero): the trace-species rule of reading R11 holds on every node."""
+    wl = W.slab(nx=nx, ny=ny, steps=steps, name="species_absent")
+    X = wl.X_init.copy()
+    X[2] = 0.0
+    wl.X_init = X / X.sum(axis=0)
+    return wl
+
+
+def closed_line(nx=30, steps=150):
+    wl = W.slab(nx=nx, ny=1, steps=steps, name="closed_line")
+    wl.bc_lo = wl.bc_hi = W.BC_BOUNCEBACK
+    return wl
+
+
+def ragged_3d(steps=20):
+    base = W.slab(nx=13, ny=7, steps=steps)
+    wl = W.slab(nx=13, ny=7, steps=steps, name="slab3d_13x7x3")
+    wl.nz = 3
+    wl.porosity = W.porosity_field((3, 7, 13), 3.0, 21)
+    wl.X_init = W.random_mole_fractions(3, wl.N, 22)
+    wl.T_init = np.full(wl.N, base.T_init[0])
+    wl.P_init = np.full(wl.N, base.P_init[0])
+    return wl
+
+
 def small_3d(steps=30):
     wl = W.anode3d(nx=14, ny=10, nz=9, steps=steps)
     return wl
@@ -63,6 +90,12 @@ CASES = {
     "slab_45x24_odd_width": lambda: W.slab(nx=45, ny=24, steps=200),
     "slab3d_m3": lambda: small_3d_m3(),
     "anode3d_m6": lambda: small_3d(),
+    # degenerate and ragged shapes
+    "line_40x1": lambda: W.slab(nx=40, ny=1, steps=150, name="line_40x1"),
+    "slab_7x5_below_one_block": lambda: W.slab(nx=7, ny=5, steps=100, name="slab_7x5"),
+    "species_absent_everywhere": lambda: species_absent(),
+    "closed_line_30x1": lambda: closed_line(),
+    "slab3d_13x7x3_ragged": lambda: ragged_3d(),
 }
 
 

@@ -177,6 +177,25 @@ def other_forms(stream, torch, lbm):
     out["capillary_256x4_fp64_2000_steps"] = {
         "ms_per_step": ms, "nodes": wl.N, "steps": wl.steps, "value": wl.N * wl.L * 1e3 / ms / 1e6, "unit": UNIT,
         "note": "1024 nodes: launch-bound; parity with the oracle in tests/test_gpu_parity.py"}
+    # a synthetic polarisation curve of the anode half-cell (Sec. 4.1): the
+    # 12 x 2 x 2 electrochemical anode slice in FP64, every point relaxed
+    # from the same saved state (6 potential updates x 20 steps)
+    from paper_2409_02930_gb300 import mea
+    wl = W.anode3d_electro(nx=12, ny=2, nz=2, steps=1)
+    g = lbm.Lattice(wl, precision=lbm.LBM_FP64, stream=sp)
+    image = g.save()
+    cell = mea.HalfCell(g, wl.nx, wl.ny, wl.nz, wl.dx, wl.mechanism.resistivity)
+    pots = [0.2, 0.25, 0.3, 0.35, 0.4, 0.45, 0.5]
+    t0 = time.perf_counter()
+    curve = cell.polarisation_curve(pots, restore=lambda: g.load_state(image), steps_per_update=20,
+                                    max_updates=6, tol=0.0)
+    sec = time.perf_counter() - t0
+    g.close()
+    out["half_cell_polarisation_fp64"] = {
+        "workload": "anode3d_electro_12x2x2", "electrode_potential_V": pots,
+        "current_density_A_per_m2": [c.current_density for c in curve], "seconds": sec,
+        "note": "synthetic mechanism; each point 120 reactive steps from the saved initial state; the curve "
+                "against the oracle's in tests/test_gpu_mea.py"}
     return out
 
 

@@ -17,8 +17,13 @@ over y and z.
 field until the electrolyte potential settles; ``potential_for_current``
 finds by the secant method the electrode potential that carries a target
 current density (the paper does this for the cathode potential, Sec. 4.1;
-here it is applied to the one electrode the lattice holds), which traces a
-polarisation curve point by point.
+here it is applied to the one electrode the lattice holds), and
+``polarisation_curve`` relaxes the cell at a list of electrode potentials.
+Both take an optional ``restore`` that puts the stepper back into one
+saved state before every relaxation (``lbm.Lattice.load_state`` of an image
+from ``save``), so that every point starts from the same state and the
+current is a function of the potential alone; without it each relaxation
+continues from where the previous one stopped.
 
 A stepper has ``step(n)``, ``current()`` (I_v per node, [N], A/m^3) and
 ``set_potential(field)`` (Phi_electrode - Phi_electrolyte per node, [N], V);
@@ -77,6 +82,13 @@ class HalfCell:
         dphi = phi_electrode - self.phi_el
         self.g.set_potential(np.broadcast_to(dphi, (self.nz, self.ny, self.nx)).reshape(-1).copy())
 
+    def reset(self, restore=None):
+        """Electrolyte potential back to zero and, with restore, the stepper
+        back to its saved state."""
+        self.phi_el = np.zeros(self.nx)
+        if restore is not None:
+            restore()
+
     def relax(self, phi_electrode: float, steps_per_update: int = 200, max_updates: int = 50,
               tol: float = 1e-6) -> CellState:
         """Steps the lattice in blocks, updating the electrolyte potential from
@@ -93,12 +105,17 @@ class HalfCell:
                 break
         return CellState(phi_electrode, Iv, Ia, self.phi_el.copy(), it)
 
+    def _point(self, phi_electrode: float, restore, relax_kw) -> CellState:
+        if restore is not None:
+            self.reset(restore)
+        return self.relax(phi_electrode, **relax_kw)
+
     def potential_for_current(self, target: float, phi0: float, phi1: float, rtol: float = 1e-3,
-                              max_iter: int = 20, **relax_kw) -> CellState:
+                              max_iter: int = 20, restore=None, **relax_kw) -> CellState:
         """Secant iteration on the electrode potential until the relaxed cell
         carries the target current density [A/m^2] within rtol."""
-        s0 = self.relax(phi0, **relax_kw)
-        s1 = self.relax(phi1, **relax_kw)
+        s0 = self._point(phi0, restore, relax_kw)
+        s1 = self._point(phi1, restore, relax_kw)
         f0, f1 = s0.current_density - target, s1.current_density - target
         for _ in range(max_iter):
             if abs(f1) <= rtol * max(abs(target), 1e-300):
@@ -107,8 +124,13 @@ class HalfCell:
                 break
             phi2 = phi1 - f1 * (phi1 - phi0) / (f1 - f0)
             phi0, f0 = phi1, f1
-            s1 = self.relax(phi2, **relax_kw)
+            s1 = self._point(phi2, restore, relax_kw)
             phi1, f1 = phi2, s1.current_density - target
         if abs(f1) <= rtol * max(abs(target), 1e-300):
             return s1
         raise RuntimeError("secant iteration on the electrode potential did not reach the target current")
+
+    def polarisation_curve(self, potentials, restore=None, **relax_kw):
+        """Relaxed cell states at each electrode potential [V] (one point of
+        the polarisation curve each)."""
+        return [self._point(float(v), restore, relax_kw) for v in potentials]

@@ -60,6 +60,51 @@ def test_relaxation_and_secant_on_a_known_current_law():
     assert abs(t.current_density / target - 1) < 1e-8
 
 
+class AgingTafelStepper(TafelStepper):
+    """A Tafel stepper whose exchange current grows with the steps taken
+    since its state was saved: without a restore, the current at a given
+    potential depends on the points taken before it."""
+
+    def __init__(self, n, growth=1e-3, **kw):
+        super().__init__(n, **kw)
+        self.growth, self.steps = growth, 0
+
+    def step(self, k):
+        self.steps += k
+
+    def current(self):
+        return (1 + self.growth * self.steps) * super().current()
+
+    def restore(self):
+        self.steps = 0
+
+
+def test_polarisation_curve_points_start_from_the_saved_state():
+    """With restore every point of the curve equals the point taken alone
+    on a fresh stepper (the same schedule from the same state); without it
+    the later points carry the steps of the earlier ones."""
+    nx, dx, om = 8, 2e-6, 0.3
+    pots = [0.01, 0.02, 0.04]
+    kw = dict(steps_per_update=5, max_updates=6, tol=0.0)
+    st = AgingTafelStepper(nx)
+    curve = mea.HalfCell(st, nx, 1, 1, dx, om).polarisation_curve(pots, restore=st.restore, **kw)
+    for v, c in zip(pots, curve):
+        alone = mea.HalfCell(AgingTafelStepper(nx), nx, 1, 1, dx, om).relax(v, **kw)
+        assert c.current_density == alone.current_density
+        np.testing.assert_array_equal(c.phi_electrolyte, alone.phi_electrolyte)
+    assert all(b.current_density > a.current_density for a, b in zip(curve, curve[1:]))
+    st2 = AgingTafelStepper(nx)
+    drift = mea.HalfCell(st2, nx, 1, 1, dx, om).polarisation_curve(pots, **kw)
+    assert drift[0].current_density == curve[0].current_density
+    assert drift[2].current_density > curve[2].current_density
+    # the secant with restore: a function of the potential alone
+    st3 = AgingTafelStepper(nx)
+    target = curve[1].current_density
+    t = mea.HalfCell(st3, nx, 1, 1, dx, om).potential_for_current(target, 0.01, 0.04, rtol=1e-10,
+                                                                  restore=st3.restore, **kw)
+    assert abs(t.phi_electrode - 0.02) < 1e-6
+
+
 class OracleStepper:
     def __init__(self, wl):
         self.o = oracle.Oracle(wl)

@@ -177,6 +177,28 @@ def other_forms(stream, torch, lbm):
     out["capillary_256x4_fp64_2000_steps"] = {
         "ms_per_step": ms, "nodes": wl.N, "steps": wl.steps, "value": wl.N * wl.L * 1e3 / ms / 1e6, "unit": UNIT,
         "note": "1024 nodes: launch-bound; parity with the oracle in tests/test_gpu_parity.py"}
+    # x-slab decomposition on one GPU: the 2048 x 2048 slab as two slabs in
+    # one process (the in-process halo exchange: device column copies on the
+    # lattice stream), one step at a time, against the undivided lattice
+    # stepped one step at a time on the same stream
+    from paper_2409_02930_gb300 import slabs as S
+    wl = W.slab(nx=2048, ny=2048, steps=20, name="slab_2048x2048")
+    g = lbm.Lattice(wl, precision=lbm.LBM_FP32, stream=sp)
+    g.step(2)
+    ms_whole = timed(lambda k: [g.step(1) for _ in range(k)], 20) / 20
+    g.close()
+    with torch.cuda.stream(stream):
+        run = S.SlabRun(wl, 2, range(2), lambda w: S.LatticeStepper(w, lbm.LBM_FP32), S.LocalExchange())
+        run.step(2)
+        ms_slabs = timed(run.step, 20) / 20
+    halo_values = sum(2 * S.HALO * (s.left is not None) + 2 * S.HALO * (s.right is not None)
+                      for s in run.slabs) * wl.L * 9 * wl.ny
+    del run
+    out["slab_2048x2048_two_slabs_one_gpu_fp32"] = {
+        "ms_per_step": ms_slabs, "undivided_ms_per_step": ms_whole, "overhead": ms_slabs / ms_whole - 1,
+        "halo_bytes_per_step": 4 * halo_values,
+        "note": "both slabs on one GPU, exchange through device column copies (read owned edge, write ghosts); "
+                "the multi-GPU form runs the same exchange over torch.distributed point-to-point"}
     # a synthetic polarisation curve of the anode half-cell (Sec. 4.1): the
     # 12 x 2 x 2 electrochemical anode slice in FP64, every point relaxed
     # from the same saved state (6 potential updates x 20 steps)

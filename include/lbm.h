@@ -212,6 +212,23 @@ int lbm_get_populations(lbm_ctx* ctx, void* buf, size_t bytes, int on_device);
 int lbm_set_populations(lbm_ctx* ctx, const void* buf, size_t bytes, int on_device);
 
 /*
+ * lbm_get_columns / lbm_set_columns -- copy the stored populations of the x
+ * columns [x0, x0 + ncols) to / from a packed caller buffer laid out
+ * [L][Q][nz][ny][ncols] in the context's precision: the halo of an x-slab
+ * decomposition, where a node's update reads the previous step's
+ * populations up to two columns away (the pull, then the isotropic
+ * gradient stencil of the moments used after Eq. 59 and Eq. 60), so two
+ * columns cross each slab boundary.
+ * bytes = L Q nz ny ncols times the value size.  Device buffers
+ * (on_device != 0) are copied asynchronously on the context's stream, in
+ * order with its steps; host buffers synchronously.  Single lattices only.
+ * Errors: LBM_ERR_ARG (null buffer, x0 < 0, ncols < 1, x0 + ncols > nx, size
+ * mismatch), LBM_ERR_STATE (batch context), LBM_ERR_CUDA.
+ */
+int lbm_get_columns(lbm_ctx* ctx, int x0, int ncols, void* buf, size_t bytes, int on_device);
+int lbm_set_columns(lbm_ctx* ctx, int x0, int ncols, const void* buf, size_t bytes, int on_device);
+
+/*
  * lbm_save / lbm_load -- checkpoint and resume the evolving state of a
  * context (single lattice or batch): the stored populations [L][Q][N] in the
  * context's precision, the surface coverages [S][N] (FP64) when it has a

@@ -2,6 +2,7 @@
 // lattice-unit conversion, device allocation and the per-step launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdio>
@@ -706,6 +707,23 @@ static int step_once(lbm_ctx* x) {
   return LBM_OK;
 }
 
+// gather (get) / scatter of the x columns [x0, x0 + ncols) of rows of nx values
+namespace {
+template <class T>
+__global__ void k_columns(T* __restrict__ pops, T* __restrict__ buf, long long rows, int nx, int x0, int ncols,
+                          int get) {
+  const long long total = rows * ncols;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / ncols;
+    const int c = (int)(i - r * ncols);
+    T* p = pops + r * nx + x0 + c;
+    if (get) buf[i] = *p;
+    else *p = buf[i];
+  }
+}
+}  // namespace
+
 // Single lattice without a surface mechanism: kGraphSteps steps from buffer
 // `cur` captured on the private capture stream into one graph (small lattices
 // are bound by the launch rate; the replay removes the per-launch host cost).
@@ -985,6 +1003,46 @@ int lbm_set_populations(lbm_ctx* x, const void* buf, size_t bytes, int on_device
                                   on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, x->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
   return e == cudaSuccess ? LBM_OK : cuda_fail(x, e, "population copy");
+}
+
+// x columns [x0, x0 + ncols) of the stored populations <-> a packed buffer
+// [L][Q][nz][ny][ncols]: L Q nz ny rows of ncols values.  Device buffers take
+// a gather / scatter kernel (rows of a few values are far below what a
+// pitched DMA copy moves efficiently), host buffers one pitched copy.
+static int column_copy(lbm_ctx* x, int x0, int ncols, void* buf, size_t bytes, int on_device, bool get) {
+  if (!x || !buf) return LBM_ERR_ARG;
+  if (x->n_cases > 0) return fail(x, LBM_ERR_STATE, "column copies: single lattices only");
+  if (ncols < 1 || x0 < 0 || x0 + ncols > x->nx) return fail(x, LBM_ERR_ARG, "column range outside the lattice");
+  const size_t rs = real_size(x);
+  const size_t rows = (size_t)x->L * x->Q * x->ny * x->nz;
+  if (bytes != rows * ncols * rs) return fail(x, LBM_ERR_ARG, "column buffer size mismatch");
+  cudaError_t e = cudaSuccess;
+  if (on_device) {
+    const long long total = (long long)rows * ncols;
+    const int grid = (int)std::min<long long>((total + 255) / 256, 152LL * 16);
+    if (rs == 8)
+      k_columns<double><<<grid, 256, 0, x->stream>>>(static_cast<double*>(x->pops[x->cur]), static_cast<double*>(buf),
+                                                     (long long)rows, x->nx, x0, ncols, get ? 1 : 0);
+    else
+      k_columns<float><<<grid, 256, 0, x->stream>>>(static_cast<float*>(x->pops[x->cur]), static_cast<float*>(buf),
+                                                    (long long)rows, x->nx, x0, ncols, get ? 1 : 0);
+    e = cudaGetLastError();
+  } else {
+    char* pops = static_cast<char*>(x->pops[x->cur]) + (size_t)x0 * rs;
+    const size_t width = (size_t)ncols * rs, pitch = (size_t)x->nx * rs;
+    e = get ? cudaMemcpy2DAsync(buf, width, pops, pitch, width, rows, cudaMemcpyDeviceToHost, x->stream)
+            : cudaMemcpy2DAsync(pops, pitch, buf, width, width, rows, cudaMemcpyHostToDevice, x->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(x->stream);
+  }
+  return e == cudaSuccess ? LBM_OK : cuda_fail(x, e, "column copy");
+}
+
+int lbm_get_columns(lbm_ctx* x, int x0, int ncols, void* buf, size_t bytes, int on_device) {
+  return column_copy(x, x0, ncols, buf, bytes, on_device, true);
+}
+
+int lbm_set_columns(lbm_ctx* x, int x0, int ncols, const void* buf, size_t bytes, int on_device) {
+  return column_copy(x, x0, ncols, const_cast<void*>(buf), bytes, on_device, false);
 }
 
 // checkpoint image: 128-byte header, populations, coverages

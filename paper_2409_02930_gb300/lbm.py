@@ -85,6 +85,9 @@ def load(path: str = LIB_PATH):
     L.lbm_get_populations.restype = ctypes.c_int
     L.lbm_set_populations.argtypes = [vp, vp, ctypes.c_size_t, ctypes.c_int]
     L.lbm_set_populations.restype = ctypes.c_int
+    for name in ("lbm_get_columns", "lbm_set_columns"):
+        getattr(L, name).argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_size_t, ctypes.c_int]
+        getattr(L, name).restype = ctypes.c_int
     L.lbm_sync.argtypes = [vp]
     L.lbm_sync.restype = ctypes.c_int
     L.lbm_info.argtypes = [vp, _dp]
@@ -336,6 +339,24 @@ class Lattice:
         dt = np.float64 if self.precision == LBM_FP64 else np.float32
         a = np.ascontiguousarray(np.asarray(p, dtype=dt)).reshape(self.L, self.Q, self.N)
         self._check(load().lbm_set_populations(self._h, a.ctypes.data, a.nbytes, 0), "lbm_set_populations")
+
+    def get_columns(self, x0: int, ncols: int, out):
+        """Populations of the x columns [x0, x0 + ncols) into `out`, a
+        contiguous [L, Q, nz, ny, ncols] buffer of the context's precision:
+        a CUDA tensor (asynchronous on the context's stream), or a numpy
+        array or CPU tensor (lbm_get_columns)."""
+        dev = int(bool(getattr(out, "is_cuda", False)))
+        nb = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
+        self._check(load().lbm_get_columns(self._h, int(x0), int(ncols), _addr(out), nb, dev), "lbm_get_columns")
+        return out
+
+    def set_columns(self, x0: int, data):
+        """Overwrite the x columns [x0, x0 + ncols) from a contiguous
+        [L, Q, nz, ny, ncols] buffer (lbm_set_columns)."""
+        dev = int(bool(getattr(data, "is_cuda", False)))
+        ncols = data.shape[-1]
+        nb = data.nbytes if isinstance(data, np.ndarray) else data.numel() * data.element_size()
+        self._check(load().lbm_set_columns(self._h, int(x0), int(ncols), _addr(data), nb, dev), "lbm_set_columns")
 
     def step_host(self, src, dst, n: int = 1):
         """Streaming step on a host-resident state (lbm_step_host): src and dst

@@ -24,8 +24,11 @@ per side and step.
 Two transports: ``DistExchange`` (torch.distributed point-to-point, one rank
 per process: NCCL between GPUs, gloo on CPU) and ``LocalExchange`` (every
 slab in one process, copies).  A stepper is any object with ``step(n)``,
-``get_state()`` returning a torch tensor [L, Q, N_local] and
-``set_state(tensor)``; ``LatticeStepper`` wraps a library context.
+``get_columns(lo, hi)`` returning the populations of its local columns
+[lo, hi) as a contiguous tensor [L, Q, nz, ny, hi - lo], and
+``set_columns(lo, data)``; only the halo columns move.  ``LatticeStepper``
+wraps a library context (lbm_get_columns / lbm_set_columns, asynchronous
+on the context's stream).
 """
 from __future__ import annotations
 
@@ -103,40 +106,31 @@ def local_workload(wl, s: Slab):
     return out
 
 
-def _columns(state, wl_local, lo: int, hi: int):
-    """View of columns [lo, hi) of a local state [L, Q, N_local]."""
-    L, Q, _ = state.shape
-    v = state.reshape(L, Q, wl_local.nz, wl_local.ny, wl_local.nx)
-    return v[..., lo:hi]
-
-
-def owned_edge(state, wl_local, s: Slab, side: str):
-    """The HALO owned columns next to a side (copied, contiguous)."""
+def owned_range(wl_local, s: Slab, side: str):
+    """Local column range of the HALO owned columns next to a side."""
     if side == "lo":
-        return _columns(state, wl_local, s.glo, s.glo + HALO).contiguous()
+        return s.glo, s.glo + HALO
     n = wl_local.nx - s.ghi
-    return _columns(state, wl_local, n - HALO, n).contiguous()
+    return n - HALO, n
 
 
-def set_ghosts(state, wl_local, s: Slab, side: str, data):
-    if side == "lo":
-        _columns(state, wl_local, 0, s.glo).copy_(data)
-    else:
-        _columns(state, wl_local, wl_local.nx - s.ghi, wl_local.nx).copy_(data)
+def ghost_start(wl_local, s: Slab, side: str) -> int:
+    """First local column of the ghosts on a side."""
+    return 0 if side == "lo" else wl_local.nx - s.ghi
 
 
 class LocalExchange:
     """Every slab in this process: the ghosts are copied from the neighbours'
     owned columns of the same step."""
 
-    def exchange(self, states, wls, slabs):
-        edges = [{side: owned_edge(st, w, s, side) for side in ("lo", "hi")}
-                 for st, w, s in zip(states, wls, slabs)]
-        for st, w, s in zip(states, wls, slabs):
+    def exchange(self, steppers, wls, slabs):
+        edges = [{side: g.get_columns(*owned_range(w, s, side)) for side in ("lo", "hi")}
+                 for g, w, s in zip(steppers, wls, slabs)]
+        for g, w, s in zip(steppers, wls, slabs):
             if s.left is not None:
-                set_ghosts(st, w, s, "lo", edges[s.left]["hi"])
+                g.set_columns(ghost_start(w, s, "lo"), edges[s.left]["hi"])
             if s.right is not None:
-                set_ghosts(st, w, s, "hi", edges[s.right]["lo"])
+                g.set_columns(ghost_start(w, s, "hi"), edges[s.right]["lo"])
 
 
 class DistExchange:
@@ -146,9 +140,10 @@ class DistExchange:
     def __init__(self, group=None):
         self.group = group
 
-    def exchange(self, states, wls, slabs):
+    def exchange(self, steppers, wls, slabs):
+        import torch
         import torch.distributed as dist
-        (st,), (w,), (s,) = states, wls, slabs
+        (g,), (w,), (s,) = steppers, wls, slabs
         recv = {}
         # two rounds, each with at most one send and one receive per rank, so
         # that messages pair up by order even when both neighbours are the
@@ -157,15 +152,15 @@ class DistExchange:
         for send_side, to, recv_side, frm in (("hi", s.right, "lo", s.left), ("lo", s.left, "hi", s.right)):
             ops = []
             if frm is not None:
-                recv[recv_side] = owned_edge(st, w, s, recv_side).clone()
+                recv[recv_side] = torch.empty_like(g.get_columns(*owned_range(w, s, recv_side)))
                 ops.append(dist.P2POp(dist.irecv, recv[recv_side], frm, self.group))
             if to is not None:
-                ops.append(dist.P2POp(dist.isend, owned_edge(st, w, s, send_side), to, self.group))
+                ops.append(dist.P2POp(dist.isend, g.get_columns(*owned_range(w, s, send_side)), to, self.group))
             if ops:
                 for req in dist.batch_isend_irecv(ops):
                     req.wait()
         for side, data in recv.items():
-            set_ghosts(st, w, s, side, data)
+            g.set_columns(ghost_start(w, s, side), data)
 
 
 class SlabRun:
@@ -184,10 +179,7 @@ class SlabRun:
         for _ in range(n):
             for g in self.steppers:
                 g.step(1)
-            states = [g.get_state() for g in self.steppers]
-            self.exchange.exchange(states, self.wls, self.slabs)
-            for g, st in zip(self.steppers, states):
-                g.set_state(st)
+            self.exchange.exchange(self.steppers, self.wls, self.slabs)
 
     def owned(self, state, k: int):
         """Owned columns of a per-node field [..., N_local] of local slab k,
@@ -199,30 +191,29 @@ class SlabRun:
 
 
 class LatticeStepper:
-    """A library context as a slab stepper; the state moves through a device
-    tensor of the context's precision (lbm_get/set_populations on device
-    pointers)."""
+    """A library context as a slab stepper.  The context runs on the torch
+    stream current at construction, so its steps, its column copies and the
+    exchange's tensor operations are ordered on one stream."""
 
     def __init__(self, wl, precision, device=None):
+        import ctypes
+
         import torch
 
         from . import lbm
-        self.lbm = lbm
-        self.g = lbm.Lattice(wl, precision=precision)
-        dt = torch.float64 if precision == lbm.LBM_FP64 else torch.float32
-        self.buf = torch.empty((self.g.L, self.g.Q, wl.N), dtype=dt,
-                               device=device if device is not None else torch.device("cuda"))
+        self.torch = torch
+        st = torch.cuda.current_stream(device)
+        self.g = lbm.Lattice(wl, precision=precision, stream=ctypes.c_void_p(st.cuda_stream))
+        self.dtype = torch.float64 if precision == lbm.LBM_FP64 else torch.float32
+        self.device = st.device
+        self.shape = (self.g.L, self.g.Q, wl.nz, wl.ny)
 
     def step(self, n: int):
         self.g.step(n)
 
-    def get_state(self):
-        L = self.lbm.load()
-        self.g._check(L.lbm_get_populations(self.g._h, self.buf.data_ptr(), self.buf.numel() * self.buf.element_size(),
-                                            1), "lbm_get_populations")
-        return self.buf
+    def get_columns(self, lo: int, hi: int):
+        out = self.torch.empty(self.shape + (hi - lo,), dtype=self.dtype, device=self.device)
+        return self.g.get_columns(lo, hi - lo, out)
 
-    def set_state(self, t):
-        L = self.lbm.load()
-        self.g._check(L.lbm_set_populations(self.g._h, t.data_ptr(), t.numel() * t.element_size(), 1),
-                      "lbm_set_populations")
+    def set_columns(self, lo: int, data):
+        self.g.set_columns(lo, data.contiguous())

@@ -21,16 +21,22 @@ from paper_2409_02930_gb300 import workloads as W  # noqa: E402
 
 class OracleStepper:
     def __init__(self, wl):
+        self.wl = wl
         self.o = oracle.Oracle(wl)
+
+    def _grid(self, p):
+        return p.reshape(self.o.nl, self.o.Q, self.wl.nz, self.wl.ny, self.wl.nx)
 
     def step(self, n):
         self.o.step(n)
 
-    def get_state(self):
-        return torch.from_numpy(self.o.pops().copy())
+    def get_columns(self, lo, hi):
+        return torch.from_numpy(np.ascontiguousarray(self._grid(self.o.pops())[..., lo:hi]))
 
-    def set_state(self, t):
-        self.o.set_pops(t.numpy())
+    def set_columns(self, lo, data):
+        p = self.o.pops().copy()
+        self._grid(p)[..., lo:lo + data.shape[-1]] = data.numpy()
+        self.o.set_pops(p)
 
 
 def cases():
@@ -58,6 +64,28 @@ def test_slabs_in_one_process_equal_the_whole_lattice(name, world):
         mine = run.owned(run.steppers[k].o.pops(), k)
         ref = global_owned(whole, wl, s)
         np.testing.assert_allclose(mine, ref, rtol=1e-13, atol=1e-13 * np.abs(ref).max())
+
+
+def test_exchange_moves_only_the_halo_columns():
+    """The in-process exchange reads the two owned columns next to each
+    inner side and writes the two ghost columns there; every other column of
+    every slab is left as it was."""
+    wl = cases()["periodic"]
+    run = S.SlabRun(wl, 3, range(3), OracleStepper, S.LocalExchange())
+    for g in run.steppers:
+        g.step(3)
+    before = [g.o.pops().copy() for g in run.steppers]
+    run.exchange.exchange(run.steppers, run.wls, run.slabs)
+    for g, w, s, b in zip(run.steppers, run.wls, run.slabs, before):
+        a = g.o.pops().reshape(g.o.nl, g.o.Q, w.nz, w.ny, w.nx)
+        b = b.reshape(a.shape)
+        changed = np.where(np.any(a != b, axis=(0, 1, 2, 3)))[0]
+        ghosts = set(range(s.glo)) | set(range(w.nx - s.ghi, w.nx))
+        assert set(changed.tolist()) <= ghosts
+        nb = run.steppers[s.left]
+        wl_l, s_l = run.wls[s.left], run.slabs[s.left]
+        left_edge = nb.o.pops().reshape(a.shape[:4] + (wl_l.nx,))[..., wl_l.nx - s_l.ghi - S.HALO:wl_l.nx - s_l.ghi]
+        np.testing.assert_array_equal(a[..., :s.glo], left_edge)
 
 
 def test_plan_splits_and_links_the_slabs():

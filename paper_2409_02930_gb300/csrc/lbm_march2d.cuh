@@ -214,6 +214,12 @@ __global__ void __launch_bounds__(TX, MINB)
   for (int k = 0; k < PD; ++k) issue(m0 - 1 + k);
   int last_issued = m0 - 1 + PD - 1;
   int aborted_at = mend + 1;
+  // Without reservoir columns the state a thread computes for its column in
+  // the ring phase of row s (from the same zeroth and first moments, in the
+  // same order) is the state the collision of row s needs one iteration
+  // later: it is kept in registers instead of being formed again.
+  constexpr bool KEEP = TMA && !INLET;
+  State<R, D, M> st_prev, st_new;
 #pragma unroll 1
   for (int s = m0 - 1; s <= mend; ++s) {
     const bool ok = landed(s);                       // row s has landed
@@ -248,6 +254,7 @@ __global__ void __launch_bounds__(TX, MINB)
 #pragma unroll
         for (int k = 0; k < M; ++k) rs[(2 * D + k) * TX] = st.Y[k];
       }
+      if (KEEP) st_new = st;
     }
     if (s + PD <= mend) {
       issue(s + PD);
@@ -286,7 +293,8 @@ __global__ void __launch_bounds__(TX, MINB)
       // this thread's ring column is its collide column (xm == xt here)
       const R* sf = static_of(buf_of(y));
       State<R, D, M> st;
-      st.template from_moments<EN, true>(p, mo, slow ? a.phi[n] : sf[0], EN ? R(0) : (slow ? a.Tfix[n] : sf[SSTR]));
+      if (KEEP) st = st_prev;
+      else st.template from_moments<EN, true>(p, mo, slow ? a.phi[n] : sf[0], EN ? R(0) : (slow ? a.Tfix[n] : sf[SSTR]));
       Grad<R, D, M, EN> gr;
       gr.divu = R(0);
 #pragma unroll
@@ -333,6 +341,7 @@ __global__ void __launch_bounds__(TX, MINB)
         collide_gen<R, D, M, EN>(p, pf, n, mo, st, gr, a.dst, a.status);
       }
     }
+    if (KEEP) st_prev = st_new;
     __syncthreads();
   }
   if (TMA && bulk) {

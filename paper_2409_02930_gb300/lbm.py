@@ -145,6 +145,12 @@ def _addr(buf) -> int:
     return int(buf.data_ptr())
 
 
+def _require_contiguous(buf):
+    ok = buf.flags["C_CONTIGUOUS"] if isinstance(buf, np.ndarray) else buf.is_contiguous()
+    if not ok:
+        raise ValueError("buffer must be contiguous")
+
+
 def _current_stream():
     try:
         import torch
@@ -345,6 +351,7 @@ class Lattice:
         contiguous [L, Q, nz, ny, ncols] buffer of the context's precision:
         a CUDA tensor (asynchronous on the context's stream), or a numpy
         array or CPU tensor (lbm_get_columns)."""
+        _require_contiguous(out)
         dev = int(bool(getattr(out, "is_cuda", False)))
         nb = out.nbytes if isinstance(out, np.ndarray) else out.numel() * out.element_size()
         self._check(load().lbm_get_columns(self._h, int(x0), int(ncols), _addr(out), nb, dev), "lbm_get_columns")
@@ -353,6 +360,7 @@ class Lattice:
     def set_columns(self, x0: int, data):
         """Overwrite the x columns [x0, x0 + ncols) from a contiguous
         [L, Q, nz, ny, ncols] buffer (lbm_set_columns)."""
+        _require_contiguous(data)
         dev = int(bool(getattr(data, "is_cuda", False)))
         ncols = data.shape[-1]
         nb = data.nbytes if isinstance(data, np.ndarray) else data.numel() * data.element_size()

@@ -144,6 +144,10 @@ class DistExchange:
         import torch
         import torch.distributed as dist
         (g,), (w,), (s,) = steppers, wls, slabs
+        # the owned edge columns next to each side with a neighbour (every
+        # edge and ghost block has the same shape: HALO columns)
+        edge = {side: g.get_columns(*owned_range(w, s, side))
+                for side, nb in (("lo", s.left), ("hi", s.right)) if nb is not None}
         recv = {}
         # two rounds, each with at most one send and one receive per rank, so
         # that messages pair up by order even when both neighbours are the
@@ -152,10 +156,10 @@ class DistExchange:
         for send_side, to, recv_side, frm in (("hi", s.right, "lo", s.left), ("lo", s.left, "hi", s.right)):
             ops = []
             if frm is not None:
-                recv[recv_side] = torch.empty_like(g.get_columns(*owned_range(w, s, recv_side)))
+                recv[recv_side] = torch.empty_like(edge[recv_side])
                 ops.append(dist.P2POp(dist.irecv, recv[recv_side], frm, self.group))
             if to is not None:
-                ops.append(dist.P2POp(dist.isend, g.get_columns(*owned_range(w, s, send_side)), to, self.group))
+                ops.append(dist.P2POp(dist.isend, edge[send_side], to, self.group))
             if ops:
                 for req in dist.batch_isend_irecv(ops):
                     req.wait()

@@ -102,7 +102,7 @@ def _declare(L):
     L.oc_get_diag.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
     L.oc_moments.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
     L.oc_moments_lane.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, _dp]
-    L.oc_set_tangents.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+    L.oc_set_tangents.argtypes = [ctypes.c_void_p, _dp, _dp, _dp, _dp]
     L.oc_set_potential.argtypes = [ctypes.c_void_p, _dp, ctypes.c_double]
     L.oc_threads.restype = ctypes.c_int
     L.oc_lanes.restype = ctypes.c_int
@@ -221,6 +221,7 @@ class Oracle:
         self.nl, self.Q, self.D = int(info[3]), int(info[4]), int(info[5])
         self.N = wl.N
         self.M = wl.M
+        self.R = int(c.R)
 
     def __del__(self):
         h = getattr(self, "_h", None)
@@ -277,10 +278,11 @@ class Oracle:
         return out
 
     # ---- dual-number build: exact directional derivatives ----------------
-    def set_tangents(self, dphi=None, dpore=None, dtort=None):
+    def set_tangents(self, dphi=None, dpore=None, dtort=None, dA=None):
         """Seed the derivative lanes: dphi [LANES][N] directions of the
         porosity field, dpore / dtort [LANES] of the pore radius [m] and the
-        tortuosity.  Resets the state to the initial equilibria."""
+        tortuosity, dA [LANES][R] of the mechanism's pre-exponential factors.
+        Resets the state to the initial equilibria and coverages."""
         K = LANES
 
         def opt(a, shape):
@@ -291,7 +293,9 @@ class Oracle:
             b[:a.shape[0]] = a.reshape((a.shape[0],) + shape[1:])
             return b
 
-        keep = [opt(dphi, (K, self.N)), opt(dpore, (K,)), opt(dtort, (K,))]
+        R = self.R
+        keep = [opt(dphi, (K, self.N)), opt(dpore, (K,)), opt(dtort, (K,)),
+                opt(dA, (K, R)) if R > 0 else None]
         self._L.oc_set_tangents(self._h, *[_ptr(a) if a is not None else None for a in keep])
 
     def pops_lane(self, lane: int) -> np.ndarray:

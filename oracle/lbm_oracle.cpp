@@ -347,7 +347,8 @@ struct Oracle {
   real rho_in[2][MMAX], T_in[2];
   // mechanism
   int S, Rn;
-  double nu_g[RMAX][MMAX], nu_s[RMAX][SMAX], Apre[RMAX], Ea[RMAX];
+  double nu_g[RMAX][MMAX], nu_s[RMAX][SMAX], Ea[RMAX];
+  real Apre[RMAX];                  // pre-exponential factors (dual build: seedable)
   real gamma, a_s, ms[SMAX], cvs[SMAX], Us0[SMAX], Ug0[MMAX];
   int edge[RMAX];
   double nel[RMAX], l_tpb, beta_ct, resist, dphi;
@@ -1267,7 +1268,7 @@ void oc_set_potential(void* h, const double* field, double uniform) {
   else o->dphi_node.clear();
 }
 
-void oc_set_tangents(void* h, const double* dphi, const double* dpore, const double* dtort) {
+void oc_set_tangents(void* h, const double* dphi, const double* dpore, const double* dtort, const double* dA) {
   Oracle* o = (Oracle*)h;
 #ifdef ORACLE_DUAL
   for (int n = 0; n < o->N; ++n)
@@ -1276,8 +1277,11 @@ void oc_set_tangents(void* h, const double* dphi, const double* dpore, const dou
     o->d0.d[k] = dpore ? 2.0 * dpore[k] / o->cfg.dx : 0.0;
     o->tort.d[k] = dtort ? dtort[k] : 0.0;
   }
+  // directions of the pre-exponential factors A_r [lane][reaction]
+  for (int r = 0; r < o->Rn; ++r)
+    for (int k = 0; k < NT; ++k) o->Apre[r].d[k] = dA ? dA[(size_t)k * o->Rn + r] : 0.0;
 #else
-  (void)dphi; (void)dpore; (void)dtort;
+  (void)dphi; (void)dpore; (void)dtort; (void)dA;
 #endif
   init_populations(o);
   for (int s = 0; s < o->S; ++s)

@@ -7,8 +7,15 @@ derivatives of the time loop), which the adjoint form is checked against.
 * derivatives of an outlet flux after many steps equal central differences
   of the plain build (porosity field, pore radius, tortuosity);
 * the Knudsen diffusivity depends on pore radius and tortuosity only
-  through their ratio, so r_p dJ/dr_p = -tau dJ/dtau exactly.
+  through their ratio, so r_p dJ/dr_p = -tau dJ/dtau exactly;
+* seeded in the pre-exponential factors A_r of a surface mechanism, the
+  derivatives of the coverages, species densities and temperature after a
+  few reactive steps equal central differences of the plain build in
+  ln A_r (the derivative of the backward-Euler extents, carried through the
+  Newton iteration in dual numbers).
 """
+import copy
+
 import numpy as np
 import pytest
 
@@ -164,3 +171,45 @@ def test_full_gradient_on_a_4x4x4_lattice_by_brute_force():
     scale = np.abs(grad).max()
     assert scale > 0
     np.testing.assert_allclose(fd, grad, rtol=0, atol=1e-6 * scale)
+
+
+def test_derivatives_in_the_pre_exponential_factors_match_central_differences():
+    """The reactive 3-D anode (20 surface steps, 8 adsorbates) on 4 x 2 x 2
+    nodes, 3 steps: lane k seeded with A_k (the derivative in ln A_k) for the
+    first LANES steps of the mechanism.  Central differences of the plain
+    build with A_k scaled by exp(+-h), h = 1e-3 (truncation ~h^2, measured
+    below 1e-6 of the field's derivative); the bound adds the differences'
+    rounding noise, 1e-13 of the field's magnitude over h.  A derivative
+    dropped anywhere on the path from A_k to the fields (the rate constant,
+    the Newton iteration, the sources) leaves the lane at zero and fails."""
+    wl = W.anode3d_reactive(nx=4, ny=2, nz=2, steps=3)
+    A = np.asarray(wl.mechanism.A, float)
+    K = oracle.LANES
+    dA = np.zeros((K, wl.mechanism.R))
+    for k in range(K):
+        dA[k, k] = A[k]
+    o = oracle.Oracle(wl, dual=True)
+    o.set_tangents(dA=dA)
+    o.step(wl.steps)
+    fields = (oracle.MOM_XS, oracle.MOM_RHO_A, oracle.MOM_T)
+    h = 1e-3
+    checked = 0
+    for k in range(K):
+        runs = []
+        for sgn in (1.0, -1.0):
+            w2 = copy.deepcopy(wl)
+            w2.mechanism.A = A.copy()
+            w2.mechanism.A[k] *= np.exp(sgn * h)
+            p = oracle.Oracle(w2)
+            p.step(wl.steps)
+            runs.append([p.moments(f) for f in fields])
+        for j, f in enumerate(fields):
+            fd = (runs[0][j] - runs[1][j]) / (2 * h)
+            lane = o.moments(f, lane=k)
+            noise = 1e-13 * np.abs(runs[0][j]).max() / h
+            err = np.abs(lane - fd).max()
+            assert err <= 1e-5 * np.abs(fd).max() + noise, (k, f, err, np.abs(fd).max())
+            if np.abs(fd).max() > 100 * noise:
+                checked += 1
+    assert checked >= 6           # the steps that act within three steps are resolved
+

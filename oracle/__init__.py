@@ -6,7 +6,8 @@ C++ loops in double precision, OpenMP over nodes) with the host compiler and
 drives it through ctypes.  It shares no code with the CUDA library.  The same
 source built with -DORACLE_DUAL carries forward-mode dual numbers: exact
 directional derivatives of the time loop with respect to the porosity field,
-pore radius and tortuosity (``Oracle(wl, dual=True)``, ``set_tangents``).
+pore radius, tortuosity and the mechanism's pre-exponential factors
+(``Oracle(wl, dual=True)``, ``set_tangents``).
 """
 from __future__ import annotations
 

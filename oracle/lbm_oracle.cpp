@@ -32,7 +32,7 @@
 // operations one for one and each derivative part applies the chain rule of
 // the operation, so the derivative parts after n steps are exact
 // Jacobian-vector products of the whole time loop with respect to the seeded
-// inputs (porosity field, pore radius, tortuosity).
+// inputs (porosity field, pore radius, tortuosity, pre-exponential factors).
 // ---------------------------------------------------------------------------
 inline double rmax(double a, double b) { return (a < b) ? b : a; }
 inline double rmin(double a, double b) { return (b < a) ? b : a; }
